@@ -1,0 +1,171 @@
+"""FP64 CPU oracle of the classical spectral TV decomposition (arXiv 2006.10004, Sec. 2).
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs
+of ``bench.py`` may import this package. The CUDA product path
+(``paper_2006_10004_gb300``) never imports it, and the two share no code.
+
+The arithmetic lives in ``tvspec_oracle.c`` (plain loops, double precision, compiled with
+``-ffp-contract=off``); this module only compiles it with gcc and marshals numpy arrays.
+
+Functions and the passages they follow:
+
+* ``grad`` / ``div``  -- forward differences with Neumann boundary and the negative adjoint
+  (the discrete form of J_TV, Eq. TV; Chambolle 2004 as cited in Sec. 4.3).
+* ``chambolle``      -- fixed-iteration Chambolle projection for one ROF step (Eq. ROF).
+* ``rof_gap``        -- duality gap of a ROF step (diagnostic).
+* ``decompose``      -- TV flow by implicit Euler (Eq. TVflow, Eq. ROF), phi (Eq. TVtrafo),
+  S(t) (Sec. 2.1), bands (Eq. spectral_bands) and residual (Eq. finite_inverse_trafo).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tvspec_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lock = threading.Lock()
+_handle = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, OpenMP, no FP contraction). Returns the .so path."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _lib():
+    global _handle
+    with _lock:
+        if _handle is None:
+            build()
+            h = ctypes.CDLL(_LIB)
+            h.orc_grad.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
+            h.orc_grad.restype = None
+            h.orc_div.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+            h.orc_div.restype = None
+            h.orc_chambolle.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
+            h.orc_chambolle.restype = ctypes.c_int
+            h.orc_rof_gap.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      _dp, _dp]
+            h.orc_rof_gap.restype = ctypes.c_double
+            h.orc_band_of.argtypes = [ctypes.c_double, _dp, ctypes.c_int]
+            h.orc_band_of.restype = ctypes.c_int
+            h.orc_decompose.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]
+            h.orc_decompose.restype = ctypes.c_int
+            h.orc_max_threads.argtypes = []
+            h.orc_max_threads.restype = ctypes.c_int
+            _handle = h
+        return _handle
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def max_threads() -> int:
+    """OpenMP threads the oracle uses (set OMP_NUM_THREADS before the first call)."""
+    return int(_lib().orc_max_threads())
+
+
+def grad(u):
+    """Forward-difference gradient (grad^1 along rows, grad^2 along columns), Neumann."""
+    u = _f64(u)
+    H, W = u.shape
+    g1 = np.empty_like(u)
+    g2 = np.empty_like(u)
+    _lib().orc_grad(_ptr(u), H, W, _ptr(g1), _ptr(g2))
+    return g1, g2
+
+
+def div(p1, p2):
+    """Discrete divergence = -grad^T."""
+    p1 = _f64(p1)
+    p2 = _f64(p2)
+    H, W = p1.shape
+    d = np.empty_like(p1)
+    _lib().orc_div(_ptr(p1), _ptr(p2), H, W, _ptr(d))
+    return d
+
+
+def chambolle(g, lam: float, n_iter: int, tau: float = 0.125, p1=None, p2=None):
+    """``n_iter`` Chambolle iterations of the ROF step with weight ``lam`` (Eq. ROF).
+
+    Returns ``(u, p1, p2)`` with ``u = g - lam div p``. ``p1``/``p2`` default to zero.
+    """
+    g = _f64(g)
+    H, W = g.shape
+    p1 = np.zeros_like(g) if p1 is None else _f64(p1).copy()
+    p2 = np.zeros_like(g) if p2 is None else _f64(p2).copy()
+    u = np.empty_like(g)
+    rc = _lib().orc_chambolle(_ptr(g), H, W, float(lam), float(tau), int(n_iter),
+                              _ptr(p1), _ptr(p2), _ptr(u))
+    if rc != 0:
+        raise MemoryError("oracle: allocation failed")
+    return u, p1, p2
+
+
+def rof_gap(g, lam: float, p1, p2) -> float:
+    """Duality gap P(u) - D(p) of the ROF step at the dual point p (|p| <= 1)."""
+    g = _f64(g)
+    p1 = _f64(p1)
+    p2 = _f64(p2)
+    H, W = g.shape
+    return float(_lib().orc_rof_gap(_ptr(g), H, W, float(lam), _ptr(p1), _ptr(p2)))
+
+
+def band_of(t: float, edges) -> int:
+    e = _f64(edges)
+    return int(_lib().orc_band_of(float(t), _ptr(e), len(e)))
+
+
+def decompose(f, dt: float, K: int, n_inner: int, edges, tau: float = 0.125,
+              warm_start: bool = True, trace: bool = False) -> dict:
+    """Spectral TV decomposition of ``f`` (H x W).
+
+    Returns a dict with ``bands`` ((n_edges-1, H, W)), ``residual`` ((H, W)), ``S`` ((K-1,))
+    and, when ``trace`` is set, ``u`` ((K+1, H, W)) holding u_0..u_K. All float64.
+    """
+    f = _f64(f)
+    if f.ndim != 2:
+        raise ValueError("f must be 2-D")
+    H, W = f.shape
+    e = _f64(edges)
+    nb = len(e) - 1
+    bands = np.zeros((nb, H, W))
+    residual = np.zeros((H, W))
+    S = np.zeros(max(K - 1, 0))
+    ut = np.zeros((K + 1, H, W)) if trace else None
+    rc = _lib().orc_decompose(_ptr(f), H, W, float(dt), int(K), int(n_inner), float(tau),
+                              1 if warm_start else 0, _ptr(e), len(e), _ptr(bands),
+                              _ptr(residual), _ptr(S), _ptr(ut) if trace else None)
+    if rc == -2:
+        raise ValueError("oracle: invalid arguments")
+    if rc != 0:
+        raise MemoryError("oracle: allocation failed")
+    out = {"bands": bands, "residual": residual, "S": S}
+    if trace:
+        out["u"] = ut
+    return out
