@@ -1,0 +1,383 @@
+"""Benchmark of the spectral TV decomposition on GB300.
+
+Default workload: one 512x512 float32 image (40 disks/rectangles + noise), K = 50 implicit
+TV-flow steps at dt = 0.5, 300 Chambolle iterations per step, 6 dyadic bands + residual.
+One bench step = one whole decomposition. Metric: Chambolle Mpx*iter/s
+(= H*W*K*n_inner / time / 1e6), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload config1|m1024|config2|config3] [--extra]
+
+Printed: one JSON line on rank 0. `value` is device-timed (inputs resident in HBM, L2
+flushed before every timed step); `e2e` is the same metric through the C ABI with host
+buffers, host<->device copies inside the timed region; `roofline` is for the dominant kernel
+(the tiled dual-iteration kernel) timed alone on the same image; `cpu_baseline` is the FP64
+oracle on this host's cores on a bounded sample of the workload.
+
+The reference arm (--impl reference) times the FP64 oracle (the only implementation of the
+method besides this one), on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+ALG_BYTES_FP32 = 20  # read p (8) + read g/lambda (4) + write p (8) per pixel per iteration
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload(name: str):
+    if name == "config1":
+        return syn.config1()
+    if name == "m1024":
+        return syn.m1024()
+    if name == "config2":
+        return syn.config2()
+    if name == "config3":
+        return syn.config3()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _oracle_sample(job, max_k: int):
+    """FP64 oracle on a bounded sample of the job: the first max_k ROF steps of the same image."""
+    import oracle
+
+    K = min(job.K, max_k)
+    t = time.perf_counter()
+    oracle.decompose(job.f, job.dt, K, job.n_inner, job.edges)
+    el = time.perf_counter() - t
+    px_it = job.f.size * K * job.n_inner
+    return px_it / el / 1e6, el, K, oracle.max_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    wl = _workload(args.workload)
+    job = wl.jobs[0]
+    kk = max(2, min(job.K, args.ref_steps_k))
+    for _ in range(args.warmup):
+        _oracle_sample(job, 2)
+    times = []
+    cores = None
+    for _ in range(args.steps):
+        v, el, K, cores = _oracle_sample(job, kk)
+        times.append(el)
+    px_it = job.f.size * kk * job.n_inner
+    value = px_it * len(times) / sum(times) / 1e6
+    sample = f"first {kk} of {job.K} ROF steps of the {job.f.shape[0]}x{job.f.shape[1]} image, {job.n_inner} iterations each"
+    line = {"impl": "reference", "metric": "Chambolle Mpx*iter/s", "value": value, "unit": "Mpx*iter/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * np.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gb300(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    import paper_2006_10004_gb300 as tv
+
+    if args.kernel_only:
+        return run_kernel_only(args, tv, torch, local)
+    wl = _workload(args.workload)
+    plan = tv.Plan(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    # ---- device-resident timed region ------------------------------------------------------
+    if args.workload == "config2":
+        jobs = [(torch.from_numpy(j.f).to(dev), j.dt, j.K, j.n_inner, j.edges) for j in wl.jobs]
+        run = lambda: plan.decompose_batch(jobs, stream=stream)
+        px_it = wl.px_iters
+        shape_desc = {"images": len(jobs)}
+    else:
+        job = wl.jobs[0]
+        f_dev = torch.from_numpy(job.f).to(dev)
+        run = lambda: plan.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream)
+        px_it = job.px_iters
+        shape_desc = {"H": job.f.shape[0], "W": job.f.shape[1], "K": job.K, "n_inner": job.n_inner,
+                      "dt": job.dt, "n_bands": len(job.edges) - 1}
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        run()
+    torch.cuda.synchronize()
+    st0 = plan.stats()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)  # evict the previous step's state from L2 (not timed)
+            evs[i][0].record(stream)
+            run()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if pg:
+        pg.barrier()
+    st1 = plan.stats()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_sec = dev_ms / 1000.0
+    if pg:
+        t = torch.tensor([t_sec], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_sec = float(t.item())
+    value = px_it * args.steps * ws / t_sec / 1e6
+    launches = int(st1["kernel_launches"] - st0["kernel_launches"])
+
+    result = {"metric": "Chambolle Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": ws,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_sec / args.steps,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+              "data": "synthetic",
+              "config": {"workload": wl.name, **shape_desc,
+                         "arith": "dual iterations f32, epilogue (u, phi, S, bands, residual) f64",
+                         "l2": "flushed before every timed step (256 MiB write, untimed)",
+                         "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                         "tile": st1["last_tile"], "temporal_block": st1["last_temporal_block"]},
+              "gpu_launches": launches, "clocks": clk.summary(),
+              "wall_s_timed_region": wall}
+
+    # ---- end to end through the C ABI with host buffers ------------------------------------
+    if not args.no_e2e and args.workload != "config2":
+        f_host = torch.from_numpy(job.f).pin_memory().numpy()
+        plan.decompose(f_host, job.dt, job.K, job.n_inner, job.edges)
+        n_e2e = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            out = plan.decompose(f_host, job.dt, job.K, job.n_inner, job.edges)
+        el = time.perf_counter() - t0
+        d2h = out["bands"].nbytes + out["residual"].nbytes + out["S"].nbytes
+        result["e2e"] = {"value": px_it * n_e2e / el / 1e6, "unit": "Mpx*iter/s",
+                         "h2d_bytes_per_step": int(job.f.nbytes), "d2h_bytes_per_step": int(d2h),
+                         "steps": n_e2e, "ms_per_step": 1000 * el / n_e2e}
+
+    # ---- roofline of the dominant kernel: dual iterations timed alone -----------------------
+    if args.workload != "config2":
+        H, W = job.f.shape
+        pitch = tv.pitch_for(W)
+        gl = torch.zeros((H, pitch), dtype=torch.float32, device=dev)
+        gl[:, :W] = torch.from_numpy(job.f / job.dt).to(dev)
+        p1 = torch.zeros_like(gl)
+        p2 = torch.zeros_like(gl)
+        iters = job.n_inner
+        plan.chambolle_iterate(gl, p1, p2, H, W, pitch, iters, stream=stream)  # tunes + warms
+        torch.cuda.synchronize()
+        s0 = plan.stats()
+        depth = max(1, s0["last_temporal_block"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            plan.chambolle_iterate(gl, p1, p2, H, W, pitch, iters, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s1 = plan.stats()
+        n_launch = int(s1["kernel_launches"] - s0["kernel_launches"])
+        per_launch_s = e0.elapsed_time(e1) / 1000.0 / max(n_launch, 1)
+        alg_bytes = ALG_BYTES_FP32 * H * W * depth
+        achieved = alg_bytes / per_launch_s / 1e9
+        peak, src = _peaks()
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tf):
+            try:
+                traffic = json.load(open(tf)).get(f"{wl.name}/tile{s1['last_tile']}/tb{depth}")
+            except Exception:
+                traffic = None
+        result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                              "frac": achieved / peak, "traffic": traffic,
+                              "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+                              "kernel": "k_tiled", "per_launch_us": per_launch_s * 1e6,
+                              "iters_per_launch": depth,
+                              "algorithmic_bytes_per_launch": alg_bytes}
+
+    # ---- CPU baseline: the FP64 oracle on this host -------------------------------------------
+    if rank == 0 and not args.no_cpu_baseline and args.workload != "config2":
+        v, el, K, cores = _oracle_sample(job, args.cpu_k)
+        result["cpu_baseline"] = {"value": v, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"first {K} of {job.K} ROF steps of the same image ({el:.1f} s)"}
+
+    if args.extra and rank == 0:
+        extra = {}
+        m = syn.m1024().jobs[0]
+        fm = torch.from_numpy(m.f).to(dev)
+        plan.decompose(fm, m.dt, m.K, m.n_inner, m.edges, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            plan.decompose(fm, m.dt, m.K, m.n_inner, m.edges, stream=stream)
+        torch.cuda.synchronize()
+        extra["m1024_decomps_per_s"] = 3 / (time.perf_counter() - t0)
+        result["extra"] = extra
+
+    if rank == 0:
+        print(json.dumps(result))
+    plan.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def run_kernel_only(args, tv, torch, local):
+    """The dual-iteration kernel alone on an N x N image (config-1 generator, shapes scaled
+    with the area): a small, self-contained case for profiler captures."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    n = args.size
+    f = syn.make_image(n, n, max(1, int(40 * n * n / 512 ** 2)), (2.0, 60.0), (0.05, 1.0), 0.02, 1000)
+    plan = tv.Plan(local, **({"kernel": tv.KERNEL_TILED, "tile": args.tile} if args.tile >= 0 else {}))
+    pitch = tv.pitch_for(n)
+    gl = torch.zeros((n, pitch), dtype=torch.float32, device=dev)
+    gl[:, :n] = torch.from_numpy(f / 0.5).to(dev)
+    p1 = torch.zeros_like(gl)
+    p2 = torch.zeros_like(gl)
+    plan.chambolle_iterate(gl, p1, p2, n, n, pitch, 8, stream=stream)
+    torch.cuda.synchronize()
+    depth = max(1, plan.stats()["last_temporal_block"])
+    iters = depth * args.launches
+    s0 = plan.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.chambolle_iterate(gl, p1, p2, n, n, pitch, iters, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s1 = plan.stats()
+    nl = int(s1["kernel_launches"] - s0["kernel_launches"])
+    us = e0.elapsed_time(e1) * 1000 / max(nl, 1)
+    alg = ALG_BYTES_FP32 * n * n * depth
+    print(json.dumps({"kernel_only": True, "size": n, "tile": s1["last_tile"], "depth": depth,
+                      "launches": nl, "per_launch_us": us, "effective_GBps": alg / (us * 1e-6) / 1e9,
+                      "Mpx_iter_per_s": n * n * depth / (us * 1e-6) / 1e6}))
+    plan.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="config1", choices=["config1", "m1024", "config2", "config3"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-k", type=int, default=50, help="ROF steps of the oracle's CPU sample")
+    ap.add_argument("--ref-steps-k", type=int, default=6, help="ROF steps per reference-arm step")
+    ap.add_argument("--extra", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time only the dual-iteration kernel on a --size x --size image")
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--launches", type=int, default=6)
+    ap.add_argument("--tile", type=int, default=-1, help="--kernel-only: fixed tile shape (-1 = autotune)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

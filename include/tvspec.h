@@ -1,0 +1,209 @@
+/*
+ * tvspec.h -- C ABI of the GB300 (sm_103a) spectral total-variation decomposition library.
+ *
+ * The library computes the classical (model-driven) spectral TV decomposition of a greyscale
+ * image (arXiv 2006.10004, Sec. 2):
+ *
+ *   u_0 = f;  u_{k+1} = argmin_v 1/2 |u_k - v|^2 + dt J_TV(v),  k = 0..K-1   (Eq. TVflow, Eq. ROF)
+ *   each ROF step solved by n_inner Chambolle projection iterations (Sec. 4.3):
+ *       w = div p - u_k/dt;  G = grad w;  p <- (p + tau G) / (1 + tau |G|);  u_{k+1} = u_k - dt div p
+ *   (forward differences, Neumann boundary, isotropic |.|, p carried across steps by default)
+ *   phi_k = t_k (u_{k+1} - 2 u_k + u_{k-1}) / dt^2,  t_k = k dt,  k = 1..K-1    (Eq. TVtrafo)
+ *   S(t_k) = sum_ij |phi_k(i,j)|                                                  (Sec. 2.1)
+ *   b^m = sum_{k: e_m <= t_k < e_{m+1}} phi_k dt                                  (Eq. spectral_bands)
+ *   f_r = u_{K-1} - t_{K-1} (u_K - u_{K-1}) / dt                                  (Eq. finite_inverse_trafo)
+ * so that sum_m b^m + f_r = f when the edges cover [0, t_{K-1}].
+ *
+ * Conventions shared by every call:
+ *   - Images are row-major float32, H rows (index i) by W columns (index j), contiguous
+ *     (row stride W) unless a pitch is given.
+ *   - The caller owns every input and output buffer. The plan owns its device workspace,
+ *     its streams and its CUDA graphs.
+ *   - No call throws or aborts. Every call returns a tvspec_status; after TVSPEC_EINVAL the
+ *     plan is unchanged and usable. tvspec_last_error() gives a one-line reason.
+ *   - Arithmetic: the dual iterations run in float32 (p may be stored as fp16/bf16 between
+ *     kernel launches, see tvspec_config.p_storage); u, phi, S, the band sums and the residual
+ *     are computed in float64. Results do not depend on the tile shape, the iterations per
+ *     kernel launch, the batch an image runs in, or graph versus plain launches (bit-identical).
+ *   - The library never falls back to CPU arithmetic: without a usable CUDA device every
+ *     compute call returns TVSPEC_ECUDA.
+ */
+#ifndef TVSPEC_H
+#define TVSPEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tvspec_plan tvspec_plan; /* opaque, owned by the library */
+
+typedef enum {
+    TVSPEC_OK = 0,
+    TVSPEC_EINVAL = 1,      /* an argument is out of range; nothing was launched */
+    TVSPEC_ENOMEM = 2,      /* device or host allocation failed, or the request exceeds the budget */
+    TVSPEC_ECUDA = 3,       /* a CUDA call failed (no device, launch failure, ...) */
+    TVSPEC_ETIMEOUT = 4,    /* a bounded wait ran out (tvspec_wait, or a device-side spin limit) */
+    TVSPEC_ENOTREADY = 5,   /* tvspec_poll: the request is still queued or running */
+    TVSPEC_ECANCELLED = 6,  /* the request was cancelled before it finished */
+    TVSPEC_ENOTSUP = 7      /* the combination of options is not supported by this build */
+} tvspec_status;
+
+/* Storage type of the dual field p between kernel launches (config.p_storage). */
+enum { TVSPEC_P_FP32 = 0, TVSPEC_P_FP16 = 1, TVSPEC_P_BF16 = 2 };
+
+/* Where the image and output pointers of a call live (mem_kind). */
+enum { TVSPEC_MEM_HOST = 0, TVSPEC_MEM_DEVICE = 1 };
+
+/* Kernel family for the dual iterations (config.kernel). */
+enum {
+    TVSPEC_KERNEL_AUTO = 0,      /* tiled kernel, tile and depth from the autotuner */
+    TVSPEC_KERNEL_NAIVE = 1,     /* one iteration per launch, one thread per pixel */
+    TVSPEC_KERNEL_TILED = 2      /* register-resident tiles, temporal blocking (tile/depth below) */
+};
+
+typedef struct {
+    int p_storage;          /* TVSPEC_P_*; default TVSPEC_P_FP32 */
+    int warm_start;         /* 1 (default): p carried from one ROF step to the next; 0: p = 0 each step */
+    float tau;              /* Chambolle step, 0 < tau <= 0.25; default 0.125 (Chambolle 2004: tau <= 1/8) */
+    int kernel;             /* TVSPEC_KERNEL_*; default TVSPEC_KERNEL_AUTO */
+    int tile;               /* tile-shape index (see tvspec_tile_info), -1 = autotune; default -1 */
+    int temporal_block;     /* dual iterations per tiled launch (1..16), 0 = autotune; default 0 */
+    int use_graphs;         /* 1 (default): replay one CUDA graph per repeated problem shape */
+    int fast_math;          /* 1 (default): hardware approximate sqrt/reciprocal; 0: IEEE-rounded */
+    size_t mem_budget_bytes;/* device memory the serving scheduler may hold; 0 = 60 GiB */
+    int max_batch;          /* serving: most requests resident at once; 0 = 256 */
+} tvspec_config;
+
+/* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in
+ * device memory of the plan's device when mem_kind == TVSPEC_MEM_DEVICE, except band_edges,
+ * which is always host memory. */
+typedef struct {
+    const float *f;         /* in:  H*W image */
+    int H, W;               /* >= 1 each; H*W <= 2^28 */
+    double dt;              /* time step = ROF weight lambda of every step; finite, > 0 */
+    int K;                  /* number of ROF steps (u_0..u_K); 2 <= K <= 100000 */
+    int n_inner;            /* Chambolle iterations per step; 0 <= n_inner <= 10^7 */
+    const double *band_edges; /* n_edges edges in t: e_0 >= 0, strictly increasing, only the last may be +inf */
+    int n_edges;            /* 2 <= n_edges <= 65 */
+    float *bands;           /* out: (n_edges-1)*H*W, band m at offset m*H*W */
+    float *residual;        /* out: H*W */
+    double *S;              /* out: K-1 values, S[k-1] = S(t_k) */
+    double *u_trace;        /* out, optional (NULL): (K+1)*H*W values of u_0..u_K in float64 */
+    int mem_kind;           /* TVSPEC_MEM_HOST or TVSPEC_MEM_DEVICE */
+} tvspec_request;
+
+typedef struct {
+    uint64_t kernel_launches;   /* kernels this plan launched (graph replays count their nodes) */
+    uint64_t graph_launches;    /* CUDA graph replays */
+    uint64_t graphs_built;      /* CUDA graphs captured and instantiated */
+    uint64_t decompositions;    /* finished decompositions */
+    size_t workspace_bytes;     /* device workspace currently held */
+    int last_tile;              /* tile-shape index used by the last tiled launch */
+    int last_temporal_block;    /* iterations per launch used by the last tiled launch */
+} tvspec_stats;
+
+/* Fill *cfg with the defaults listed above. */
+void tvspec_config_init(tvspec_config *cfg);
+
+/* Create a plan bound to CUDA device `device`. cfg may be NULL (defaults). On success *out
+ * receives the plan. Errors: EINVAL (bad cfg or out == NULL), ECUDA (no such device). */
+tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_plan **out);
+
+/* Stop the serving thread (cancelling queued requests), free the workspace and graphs, and
+ * free the plan. NULL is a no-op. */
+tvspec_status tvspec_plan_destroy(tvspec_plan *plan);
+
+/* Host-only argument check of one request; launches nothing and needs no GPU.
+ * Returns OK or EINVAL. With mem_kind == TVSPEC_MEM_HOST it also rejects a non-finite f. */
+tvspec_status tvspec_validate(const tvspec_request *req);
+
+/* One decomposition (the plain path). `stream` is a cudaStream_t (NULL = the plan's stream).
+ * With TVSPEC_MEM_HOST the call copies f in, runs, copies the outputs back and returns when
+ * they are in host memory. With TVSPEC_MEM_DEVICE the call enqueues the work on `stream` and
+ * returns; the outputs are valid once the stream reaches that point, and the next call on this
+ * plan must use the same stream (or synchronise first) because it reuses the workspace.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+tvspec_status tvspec_decompose(tvspec_plan *plan, const float *f, int H, int W, double dt, int K,
+                               int n_inner, const double *band_edges, int n_edges, float *bands,
+                               float *residual, double *S, int mem_kind, void *stream);
+
+/* Same as tvspec_decompose for one request struct (adds the optional u_trace output). */
+tvspec_status tvspec_decompose_ex(tvspec_plan *plan, const tvspec_request *req, void *stream);
+
+/* n independent decompositions of mixed sizes and schedules, run together: every launch
+ * covers the tiles of all images still inside their own K steps (Sec. 4.3 timing protocol is
+ * per image; batching only shares the GPU). Each result is bit-identical to the same request
+ * run alone. All requests must share one mem_kind. Synchronous for TVSPEC_MEM_HOST. */
+tvspec_status tvspec_decompose_batch(tvspec_plan *plan, int n, const tvspec_request *reqs,
+                                     void *stream);
+
+/* Serving (continuous batching). submit copies the request descriptor (not the buffers, which
+ * must stay valid until poll returns OK) and returns a ticket at once. A scheduler thread
+ * admits requests while their device memory fits mem_budget_bytes, runs one ROF step of every
+ * resident request per scheduler tick, retires finished requests and admits waiting ones at
+ * step boundaries. Results are bit-identical to tvspec_decompose_ex of the same request.
+ * Only TVSPEC_MEM_HOST requests are accepted. Thread-safe. */
+tvspec_status tvspec_submit(tvspec_plan *plan, const tvspec_request *req, uint64_t *ticket);
+
+/* OK when the request finished (outputs written), ENOTREADY while queued or running,
+ * ECANCELLED, or the request's own error status. EINVAL for an unknown ticket. A finished
+ * ticket stays queryable until the plan is destroyed. Thread-safe. */
+tvspec_status tvspec_poll(tvspec_plan *plan, uint64_t ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for the request; returns like tvspec_poll, or
+ * ETIMEOUT. Thread-safe. */
+tvspec_status tvspec_wait(tvspec_plan *plan, uint64_t ticket, int timeout_ms);
+
+/* Cancel a queued or running request; it is retired at the next step boundary with
+ * ECANCELLED. OK, or EINVAL for an unknown or already finished ticket. */
+tvspec_status tvspec_cancel(tvspec_plan *plan, uint64_t ticket);
+
+/* Latency statistics of finished served requests since the plan was created (or the last
+ * reset): count, p50 and p99 of submit-to-finish time in milliseconds. */
+tvspec_status tvspec_serving_stats(tvspec_plan *plan, int reset, uint64_t *count, double *p50_ms,
+                                   double *p99_ms);
+
+/* One ROF step (Eq. ROF) by n_iter Chambolle iterations on the plan's kernel: u = g - lambda div p.
+ * g (H*W), p1/p2 (H*W, in: starting dual field, out: final) and u (H*W, out) are contiguous
+ * float32 buffers in host or device memory per mem_kind. Synchronous for host memory.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENOTSUP (p_storage other than fp32). */
+tvspec_status tvspec_rof_step(tvspec_plan *plan, const float *g, int H, int W, double lambda,
+                              int n_iter, float *p1, float *p2, float *u, int mem_kind,
+                              void *stream);
+
+/* The dual iterations alone, on pitched device buffers, as the decomposition runs them:
+ * n_iter iterations of p <- (p + tau G)/(1 + tau|G|), G = grad(div p - gl), with gl = g/lambda
+ * precomputed by the caller. gl, p1, p2: device float32, row stride `pitch` elements
+ * (pitch >= W, pitch % 4 == 0, 16-byte aligned base; columns W..pitch-1 must hold zeros).
+ * Enqueued on `stream`, asynchronous. Used to time the hot kernel in isolation.
+ * Errors: EINVAL, ECUDA, ENOTSUP (p_storage other than fp32). */
+tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float *p1, float *p2,
+                                       int H, int W, int pitch, int n_iter, void *stream);
+
+/* Number of tile shapes this build provides for TVSPEC_KERNEL_TILED, and the geometry of
+ * shape `index`: columns per lane, rows per thread, warps per block, maximum iterations per
+ * launch. Returns EINVAL for an index out of range. */
+int tvspec_tile_count(void);
+tvspec_status tvspec_tile_info(int index, int *cols_per_lane, int *rows_per_thread, int *warps,
+                               int *max_temporal_block);
+
+/* Counters of this plan (see tvspec_stats). */
+tvspec_status tvspec_plan_stats(tvspec_plan *plan, tvspec_stats *out);
+
+/* Human-readable name of a status code (static storage). */
+const char *tvspec_status_str(tvspec_status status);
+
+/* Reason for the last non-OK status returned on this plan (plan may be NULL for calls that
+ * failed before a plan existed); thread-local, static storage until the next call. */
+const char *tvspec_last_error(void);
+
+/* Library version string (static storage). */
+const char *tvspec_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVSPEC_H */

@@ -1,0 +1,357 @@
+"""Python binding of the GB300 spectral TV decomposition library (``include/tvspec.h``).
+
+Argument marshalling only: every step of the decomposition runs in the CUDA kernels of
+``libtvspec.so``. There is no CPU fallback; if the library or a CUDA device is missing, the
+calls raise.
+
+Host arrays (numpy) use the host-memory mode of the C ABI; CUDA tensors (torch) use the
+device-memory mode on the current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["Plan", "Config", "TvSpecError", "load", "build", "STATUS"]
+
+STATUS = {0: "TVSPEC_OK", 1: "TVSPEC_EINVAL", 2: "TVSPEC_ENOMEM", 3: "TVSPEC_ECUDA",
+          4: "TVSPEC_ETIMEOUT", 5: "TVSPEC_ENOTREADY", 6: "TVSPEC_ECANCELLED", 7: "TVSPEC_ENOTSUP"}
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTREADY, ECANCELLED, ENOTSUP = range(8)
+P_FP32, P_FP16, P_BF16 = 0, 1, 2
+MEM_HOST, MEM_DEVICE = 0, 1
+KERNEL_AUTO, KERNEL_NAIVE, KERNEL_TILED = 0, 1, 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+class TvSpecError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({detail})")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("p_storage", ctypes.c_int), ("warm_start", ctypes.c_int), ("tau", ctypes.c_float),
+                ("kernel", ctypes.c_int), ("tile", ctypes.c_int), ("temporal_block", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("fast_math", ctypes.c_int),
+                ("mem_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("dt", ctypes.c_double), ("K", ctypes.c_int), ("n_inner", ctypes.c_int),
+                ("band_edges", ctypes.c_void_p), ("n_edges", ctypes.c_int),
+                ("bands", ctypes.c_void_p), ("residual", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("u_trace", ctypes.c_void_p), ("mem_kind", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
+                ("graphs_built", ctypes.c_uint64), ("decompositions", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_size_t), ("last_tile", ctypes.c_int),
+                ("last_temporal_block", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes) for every entry point of include/tvspec.h
+_SIGS = {
+    "tvspec_config_init": (None, [ctypes.POINTER(Config)]),
+    "tvspec_plan_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "tvspec_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "tvspec_validate": (ctypes.c_int, [ctypes.POINTER(Request)]),
+    "tvspec_decompose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_void_p]),
+    "tvspec_decompose_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_void_p]),
+    "tvspec_decompose_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Request),
+                                              ctypes.c_void_p]),
+    "tvspec_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "tvspec_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "tvspec_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]),
+    "tvspec_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "tvspec_serving_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                            _dp, _dp]),
+    "tvspec_rof_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "tvspec_chambolle_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_void_p]),
+    "tvspec_tile_count": (ctypes.c_int, []),
+    "tvspec_tile_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "tvspec_plan_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "tvspec_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "tvspec_last_error": (ctypes.c_char_p, []),
+    "tvspec_version": (ctypes.c_char_p, []),
+}
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libtvspec.so`` (building it first if needed). Raises if it cannot be built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB) or (build_if_missing and not _build.up_to_date()):
+                if not build_if_missing:
+                    raise RuntimeError(f"{_build.LIB} is missing; run __graft_entry__.build()")
+                _build.build()
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+        return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        detail = load().tvspec_last_error()
+        raise TvSpecError(status, where, detail.decode() if detail else "")
+
+
+def tile_shapes() -> list:
+    L = load()
+    out = []
+    for i in range(L.tvspec_tile_count()):
+        v, r, w, tb = (ctypes.c_int() for _ in range(4))
+        _check(L.tvspec_tile_info(i, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w), ctypes.byref(tb)),
+               "tvspec_tile_info")
+        out.append({"V": v.value, "R": r.value, "RW": w.value, "TB": tb.value})
+    return out
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+def _stream_ptr(stream) -> int:
+    """cudaStream_t of a torch stream (None: torch's current stream).
+
+    torch's default stream is the legacy NULL stream, whose handle is 0; the C ABI reads a NULL
+    stream as "the plan's own stream", so it is passed as cudaStreamLegacy (handle 1) instead.
+    """
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    ptr = int(getattr(stream, "cuda_stream", stream))
+    return ptr if ptr != 0 else 1
+
+
+class Result(dict):
+    """bands (n_bands, H, W), residual (H, W), S (K-1,), optional u (K+1, H, W)."""
+
+
+class Plan:
+    """A tvspec plan bound to one CUDA device."""
+
+    def __init__(self, device: int = 0, **cfg):
+        L = load()
+        c = Config()
+        L.tvspec_config_init(ctypes.byref(c))
+        for k, v in cfg.items():
+            if not hasattr(c, k):
+                raise TypeError(f"unknown config field {k}")
+            setattr(c, k, v)
+        self.config = c
+        h = ctypes.c_void_p()
+        _check(L.tvspec_plan_create(ctypes.byref(c), int(device), ctypes.byref(h)), "tvspec_plan_create")
+        self._h = h
+        self._lib = L
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tvspec_plan_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- request marshalling -----------------------------------------------------------------
+    @staticmethod
+    def _edges(edges) -> np.ndarray:
+        return np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+
+    def _make_request(self, f, dt, K, n_inner, edges, trace, keep):
+        e = self._edges(edges)
+        keep.append(e)
+        nb = len(e) - 1
+        if _is_torch_cuda(f):
+            import torch
+
+            f = f.contiguous()
+            if f.dtype != torch.float32 or f.dim() != 2:
+                raise TypeError("f must be a 2-D float32 CUDA tensor")
+            H, W = f.shape
+            dev = f.device
+            out = Result(bands=torch.empty((nb, H, W), dtype=torch.float32, device=dev),
+                         residual=torch.empty((H, W), dtype=torch.float32, device=dev),
+                         S=torch.empty((max(K - 1, 0),), dtype=torch.float64, device=dev))
+            if trace:
+                out["u"] = torch.empty((K + 1, H, W), dtype=torch.float64, device=dev)
+            ptr = lambda t: t.data_ptr()
+            kind = MEM_DEVICE
+        else:
+            f = np.ascontiguousarray(np.asarray(f, dtype=np.float32))
+            if f.ndim != 2:
+                raise TypeError("f must be 2-D")
+            H, W = f.shape
+            out = Result(bands=np.zeros((nb, H, W), np.float32), residual=np.zeros((H, W), np.float32),
+                         S=np.zeros((max(K - 1, 0),), np.float64))
+            if trace:
+                out["u"] = np.zeros((K + 1, H, W), np.float64)
+            ptr = lambda a: a.ctypes.data
+            kind = MEM_HOST
+        keep.append(f)
+        r = Request(f=ptr(f), H=H, W=W, dt=float(dt), K=int(K), n_inner=int(n_inner),
+                    band_edges=e.ctypes.data, n_edges=len(e), bands=ptr(out["bands"]),
+                    residual=ptr(out["residual"]), S=ptr(out["S"]) if K > 1 else ptr(out["residual"]),
+                    u_trace=ptr(out["u"]) if trace else None, mem_kind=kind)
+        return r, out, kind
+
+    def decompose(self, f, dt: float, K: int, n_inner: int, edges, trace: bool = False, stream=None):
+        """Decompose one image; returns a Result (numpy for host input, torch for CUDA input)."""
+        keep = []
+        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep)
+        st = _stream_ptr(stream) if kind == MEM_DEVICE else None
+        _check(self._lib.tvspec_decompose_ex(self._h, ctypes.byref(r), st), "tvspec_decompose_ex")
+        return out
+
+    def decompose_raw(self, f_ptr, H, W, dt, K, n_inner, edges, bands_ptr, residual_ptr, S_ptr,
+                      mem_kind, stream=0):
+        """The plain C entry with caller-owned buffers (pointers as integers)."""
+        e = self._edges(edges)
+        _check(self._lib.tvspec_decompose(self._h, f_ptr, H, W, float(dt), K, n_inner, e.ctypes.data,
+                                          len(e), bands_ptr, residual_ptr, S_ptr, mem_kind, stream),
+               "tvspec_decompose")
+
+    def decompose_batch(self, jobs, trace: bool = False, stream=None):
+        """jobs: iterable of (f, dt, K, n_inner, edges). Returns a list of Results."""
+        keep = []
+        reqs, outs, kinds = [], [], set()
+        for (f, dt, K, n_inner, edges) in jobs:
+            r, o, k = self._make_request(f, dt, K, n_inner, edges, trace, keep)
+            reqs.append(r)
+            outs.append(o)
+            kinds.add(k)
+        if len(kinds) != 1:
+            raise TypeError("all images of a batch must be host arrays or all CUDA tensors")
+        arr = (Request * len(reqs))(*reqs)
+        st = _stream_ptr(stream) if MEM_DEVICE in kinds else None
+        _check(self._lib.tvspec_decompose_batch(self._h, len(reqs), arr, st), "tvspec_decompose_batch")
+        return outs
+
+    # ---- serving -------------------------------------------------------------------------------
+    def submit(self, f, dt, K, n_inner, edges, trace: bool = False):
+        """Queue one host-memory request; returns (ticket, Result). Keep the Result alive."""
+        keep = []
+        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep)
+        if kind != MEM_HOST:
+            raise TypeError("serving takes host (numpy) images")
+        t = ctypes.c_uint64()
+        _check(self._lib.tvspec_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "tvspec_submit")
+        self._keep[t.value] = (keep, out)
+        return t.value, out
+
+    def poll(self, ticket: int) -> int:
+        return int(self._lib.tvspec_poll(self._h, ctypes.c_uint64(ticket)))
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        s = int(self._lib.tvspec_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms)))
+        if s not in (ENOTREADY, ETIMEOUT):
+            self._keep.pop(ticket, None)
+        return s
+
+    def cancel(self, ticket: int) -> int:
+        return int(self._lib.tvspec_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def serving_stats(self, reset: bool = False):
+        n = ctypes.c_uint64()
+        p50 = ctypes.c_double()
+        p99 = ctypes.c_double()
+        _check(self._lib.tvspec_serving_stats(self._h, 1 if reset else 0, ctypes.byref(n), ctypes.byref(p50),
+                                              ctypes.byref(p99)), "tvspec_serving_stats")
+        return {"count": n.value, "p50_ms": p50.value, "p99_ms": p99.value}
+
+    # ---- lower-level entry points ------------------------------------------------------------
+    def rof_step(self, g, lam: float, n_iter: int, p1=None, p2=None, stream=None):
+        """One ROF step by n_iter dual iterations; returns (u, p1, p2) (float32)."""
+        if _is_torch_cuda(g):
+            import torch
+
+            g = g.contiguous().float()
+            p1 = torch.zeros_like(g) if p1 is None else p1.contiguous().float().clone()
+            p2 = torch.zeros_like(g) if p2 is None else p2.contiguous().float().clone()
+            u = torch.empty_like(g)
+            ptr = lambda t: t.data_ptr()
+            kind, st = MEM_DEVICE, _stream_ptr(stream)
+        else:
+            g = np.ascontiguousarray(np.asarray(g, np.float32))
+            p1 = np.zeros_like(g) if p1 is None else np.array(p1, np.float32, copy=True, order="C")
+            p2 = np.zeros_like(g) if p2 is None else np.array(p2, np.float32, copy=True, order="C")
+            u = np.empty_like(g)
+            ptr = lambda a: a.ctypes.data
+            kind, st = MEM_HOST, None
+        H, W = g.shape
+        _check(self._lib.tvspec_rof_step(self._h, ptr(g), H, W, float(lam), int(n_iter), ptr(p1), ptr(p2),
+                                         ptr(u), kind, st), "tvspec_rof_step")
+        return u, p1, p2
+
+    def chambolle_iterate(self, gl, p1, p2, H: int, W: int, pitch: int, n_iter: int, stream=None):
+        """Dual iterations on pitched CUDA tensors (gl, p1, p2 of H*pitch float32), in place."""
+        _check(self._lib.tvspec_chambolle_iterate(self._h, gl.data_ptr(), p1.data_ptr(), p2.data_ptr(), H, W,
+                                                  pitch, int(n_iter), _stream_ptr(stream)),
+               "tvspec_chambolle_iterate")
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.tvspec_plan_stats(self._h, ctypes.byref(s)), "tvspec_plan_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def validate(f_shape, dt, K, n_inner, edges, f=None, mem_kind=MEM_HOST) -> int:
+    """Host-only argument check through tvspec_validate (no GPU needed); returns the status."""
+    L = load()
+    H, W = f_shape
+    e = np.ascontiguousarray(np.asarray(edges, np.float64))
+    fa = np.zeros((H, W), np.float32) if f is None else np.ascontiguousarray(np.asarray(f, np.float32))
+    dummy = np.zeros(max(1, (len(e) - 1) * H * W), np.float32)
+    S = np.zeros(max(1, K), np.float64)
+    r = Request(f=fa.ctypes.data, H=H, W=W, dt=float(dt), K=int(K), n_inner=int(n_inner),
+                band_edges=e.ctypes.data, n_edges=len(e), bands=dummy.ctypes.data, residual=dummy.ctypes.data,
+                S=S.ctypes.data, u_trace=None, mem_kind=mem_kind)
+    return int(L.tvspec_validate(ctypes.byref(r)))
+
+
+def pitch_for(W: int) -> int:
+    return int(math.ceil(W / 4) * 4)

@@ -1,0 +1,256 @@
+// Kernels around the hot loop: the reference one-iteration kernel, the start of a
+// decomposition, the per-step float64 epilogue and the standalone ROF helpers.
+#include "chambolle_math.cuh"
+#include "tvspec_internal.h"
+
+namespace tvspec {
+
+// ---------------------------------------------------------------------------------------------
+// Reference dual-iteration kernel: one Chambolle iteration per launch, one thread per pixel,
+// neighbours read from global memory, p_in -> p_out (Chambolle 2004 as used in Sec. 4.3).
+// ---------------------------------------------------------------------------------------------
+template <typename P, bool FAST>
+__global__ void __launch_bounds__(256)
+    k_naive(const P *__restrict__ p1i, const P *__restrict__ p2i, P *__restrict__ p1o,
+            P *__restrict__ p2o, const float *__restrict__ gl, int H, int W, int pitch,
+            float tau) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= H || j >= W) return;
+    auto P1 = [&](int y, int x) { return PStore<P>::load(p1i[(size_t)y * pitch + x]); };
+    auto P2 = [&](int y, int x) { return PStore<P>::load(p2i[(size_t)y * pitch + x]); };
+    auto w_at = [&](int y, int x) {
+        const float p1u = y > 0 ? P1(y - 1, x) : 0.0f;
+        const float p2l = x > 0 ? P2(y, x - 1) : 0.0f;
+        return tv_w(P1(y, x), p1u, P2(y, x), p2l, gl[(size_t)y * pitch + x]);
+    };
+    const float w = w_at(i, j);
+    const float G1 = (i < H - 1) ? __fsub_rn(w_at(i + 1, j), w) : 0.0f;
+    const float G2 = (j < W - 1) ? __fsub_rn(w_at(i, j + 1), w) : 0.0f;
+    float a = P1(i, j), b = P2(i, j);
+    tv_update<FAST>(a, b, G1, G2, tau);
+    p1o[(size_t)i * pitch + j] = PStore<P>::store(a);
+    p2o[(size_t)i * pitch + j] = PStore<P>::store(b);
+}
+
+template <typename P>
+static cudaError_t naive_typed(bool fast, const void *p1i, const void *p2i, void *p1o,
+                               void *p2o, const float *gl, int H, int W, int pitch, float tau,
+                               cudaStream_t st) {
+    dim3 block(32, 8);
+    dim3 grid((W + 31) / 32, (H + 7) / 8);
+    if (fast)
+        k_naive<P, true><<<grid, block, 0, st>>>((const P *)p1i, (const P *)p2i, (P *)p1o,
+                                                 (P *)p2o, gl, H, W, pitch, tau);
+    else
+        k_naive<P, false><<<grid, block, 0, st>>>((const P *)p1i, (const P *)p2i, (P *)p1o,
+                                                  (P *)p2o, gl, H, W, pitch, tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,
+                         void *p1_out, void *p2_out, const float *gl, int H, int W, int pitch,
+                         float tau, cudaStream_t st) {
+    switch (p_storage) {
+        case 0: return naive_typed<float>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
+        case 1: return naive_typed<__half>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
+        case 2: return naive_typed<__nv_bfloat16>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Epilogue block mapping: block b of a launch belongs to image ep_img[b]; its local index is
+// b - ep_base[img]; local block lb covers row lb / nbx, columns (lb % nbx) * kEpBlock + [0, 256).
+// The partition depends only on (H, W), so a per-image reduction over it has the same order
+// whether the image runs alone or in a batch.
+// ---------------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kEpBlock)
+    k_init(ImgDesc *__restrict__ descs, const int *__restrict__ ep_img,
+           const int *__restrict__ ep_base) {
+    const int b = blockIdx.x;
+    const int img = ep_img[b];
+    ImgDesc *d = descs + img;
+    const int lb = b - ep_base[img];
+    const int W = d->W;
+    const int nbx = (W + kEpBlock - 1) / kEpBlock;
+    const int i = lb / nbx;
+    const int j = (lb % nbx) * kEpBlock + threadIdx.x;
+    if (j >= W) return;
+    const size_t n = (size_t)i * W + j;
+    const float fv = d->f[n];
+    if (!isfinite(fv)) atomicOr(d->status, kStatusNonFinite);
+    const double u0 = (double)fv;                      // u_0 = f  (Eq. TVflow)
+    d->ua[n] = u0;
+    d->gl[(size_t)i * d->pitch + j] = (float)(u0 * d->inv_dt);
+    if (d->u_trace) d->u_trace[n] = u0;
+}
+
+cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_base,
+                        int n_blocks, cudaStream_t st) {
+    if (n_blocks <= 0) return cudaSuccess;
+    k_init<<<n_blocks, kEpBlock, 0, st>>>(const_cast<ImgDesc *>(descs), ep_img, ep_base);
+    return cudaGetLastError();
+}
+
+// Fixed-order block sum of a double (warp shuffle tree, then the first warp over the warps).
+__device__ __forceinline__ double block_sum(double v, double *s_red) {
+    constexpr unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = (lane < (int)(blockDim.x >> 5)) ? s_red[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(FULL, t, off);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// One step's epilogue, per pixel, all in float64 (Sec. 2.1-2.2):
+//   u_{k+1} = u_k - dt div p                 (Chambolle's primal recovery of the ROF step)
+//   gl      = u_{k+1} / dt                    (data term of the next step's dual iterations)
+//   phi_k   = t_k (u_{k+1} - 2 u_k + u_{k-1}) / dt^2, t_k = k dt, for k >= 1   (Eq. TVtrafo)
+//   S(t_k)  = sum |phi_k|                     (deterministic two-level reduction)
+//   b^m    += phi_k dt for the band m of t_k; a finished band is written out as float32
+//   f_r     = u_{K-1} - t_{K-1} (u_K - u_{K-1}) / dt at the last step (Eq. finite_inverse_trafo)
+template <typename P>
+__global__ void __launch_bounds__(kEpBlock)
+    k_epilogue(ImgDesc *__restrict__ descs, const int *__restrict__ ep_img,
+               const int *__restrict__ ep_base, int gstep, int depth) {
+    __shared__ double s_red[kEpBlock / 32];
+    __shared__ int s_last;
+    const int b = blockIdx.x;
+    const int img = ep_img[b];
+    ImgDesc *d = descs + img;
+    const int k = gstep - d->s0;
+    if (k < 0 || k >= d->K) return;  // uniform over the block
+    const int lb = b - ep_base[img];
+    const int H = d->H, W = d->W, pitch = d->pitch;
+    const int nbx = (W + kEpBlock - 1) / kEpBlock;
+    const int i = lb / nbx;
+    const int j = (lb % nbx) * kEpBlock + threadIdx.x;
+    const size_t N = (size_t)H * W;
+    double absphi = 0.0;
+    if (j < W) {
+        // the copy of p written by the step's last launch
+        const int cp = p_copy(k + 1, launches_per_step(d->n_inner, depth), 0);
+        const P *p1 = static_cast<const P *>(d->p1[cp]);
+        const P *p2 = static_cast<const P *>(d->p2[cp]);
+        const size_t o = (size_t)i * pitch + j;
+        const size_t n = (size_t)i * W + j;
+        // div p with the adjoint boundary terms (negative adjoint of the forward gradient)
+        const double a = (i < H - 1 ? (double)PStore<P>::load(p1[o]) : 0.0) -
+                         (i > 0 ? (double)PStore<P>::load(p1[o - pitch]) : 0.0);
+        const double c = (j < W - 1 ? (double)PStore<P>::load(p2[o]) : 0.0) -
+                         (j > 0 ? (double)PStore<P>::load(p2[o - 1]) : 0.0);
+        double *ucur = (k & 1) ? d->ub : d->ua;
+        double *uoth = (k & 1) ? d->ua : d->ub;  // u_{k-1} in, u_{k+1} out
+        const double uc = ucur[n];
+        const double un = uc - d->dt * (a + c);
+        if (!isfinite(un)) atomicOr(d->status, kStatusNonFinite);
+        d->gl[o] = (float)(un * d->inv_dt);
+        if (d->u_trace) d->u_trace[(size_t)(k + 1) * N + n] = un;
+        if (k >= 1) {
+            const double up = uoth[n];
+            const double tk = (double)k * d->dt;
+            const double phi = tk * (un - 2.0 * uc + up) * (d->inv_dt * d->inv_dt);
+            absphi = fabs(phi);
+            const int m = d->band_of_k[k];
+            const int mp = (k >= 2) ? d->band_of_k[k - 1] : -1;
+            double acc = 0.0;
+            if (mp >= 0) {
+                const double old = d->acc[n];
+                if (mp == m) acc = old;
+                else d->bands[(size_t)mp * N + n] = (float)old;  // band mp is complete
+            }
+            if (m >= 0) acc += phi * d->dt;
+            if (k == d->K - 1) {
+                if (m >= 0) d->bands[(size_t)m * N + n] = (float)acc;
+                d->residual[n] = (float)(uc - tk * (un - uc) * d->inv_dt);
+            } else {
+                d->acc[n] = acc;
+            }
+        }
+        uoth[n] = un;
+    }
+    if (k < 1) return;  // no phi at step 0
+    const double bsum = block_sum(absphi, s_red);
+    if (threadIdx.x == 0) {
+        d->partials[lb] = bsum;
+        __threadfence();
+        const unsigned prev = atomicAdd(d->counter, 1u);
+        s_last = (prev == (unsigned)d->ep_blocks - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // last block of this image: sum the partials in block order (fixed) -> S(t_k)
+    __threadfence();
+    double t = 0.0;
+    const volatile double *parts = d->partials;
+    for (int q = threadIdx.x; q < d->ep_blocks; q += kEpBlock) t += parts[q];
+    const double tot = block_sum(t, s_red);
+    if (threadIdx.x == 0) {
+        d->S[k - 1] = tot;
+        *d->counter = 0u;
+    }
+}
+
+cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_img,
+                            const int *ep_base, int n_blocks, int gstep, int depth,
+                            cudaStream_t st) {
+    if (n_blocks <= 0) return cudaSuccess;
+    ImgDesc *dd = const_cast<ImgDesc *>(descs);
+    switch (p_storage) {
+        case 0: k_epilogue<float><<<n_blocks, kEpBlock, 0, st>>>(dd, ep_img, ep_base, gstep, depth); break;
+        case 1: k_epilogue<__half><<<n_blocks, kEpBlock, 0, st>>>(dd, ep_img, ep_base, gstep, depth); break;
+        case 2: k_epilogue<__nv_bfloat16><<<n_blocks, kEpBlock, 0, st>>>(dd, ep_img, ep_base, gstep, depth); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Standalone ROF step helpers.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_gl_from_g(const float *__restrict__ g, float *__restrict__ gl, int H, int W,
+                            int pitch, double inv_lam) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= W) return;
+    gl[(size_t)i * pitch + j] = (float)((double)g[(size_t)i * W + j] * inv_lam);
+}
+
+cudaError_t launch_gl_from_g(const float *g, float *gl, int H, int W, int pitch, double lambda,
+                             cudaStream_t st) {
+    dim3 grid((W + 255) / 256, H);
+    k_gl_from_g<<<grid, 256, 0, st>>>(g, gl, H, W, pitch, 1.0 / lambda);
+    return cudaGetLastError();
+}
+
+__global__ void k_rof_primal(const float *__restrict__ p1, const float *__restrict__ p2,
+                             int pitch, const float *__restrict__ g, float *__restrict__ u,
+                             int H, int W, double lambda) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= W) return;
+    const size_t o = (size_t)i * pitch + j;
+    const double a = (i < H - 1 ? (double)p1[o] : 0.0) - (i > 0 ? (double)p1[o - pitch] : 0.0);
+    const double c = (j < W - 1 ? (double)p2[o] : 0.0) - (j > 0 ? (double)p2[o - 1] : 0.0);
+    const size_t n = (size_t)i * W + j;
+    u[n] = (float)((double)g[n] - lambda * (a + c));
+}
+
+cudaError_t launch_rof_primal(const float *p1, const float *p2, int pitch, const float *g,
+                              float *u, int H, int W, double lambda, cudaStream_t st) {
+    dim3 grid((W + 255) / 256, H);
+    k_rof_primal<<<grid, 256, 0, st>>>(p1, p2, pitch, g, u, H, W, lambda);
+    return cudaGetLastError();
+}
+
+}  // namespace tvspec

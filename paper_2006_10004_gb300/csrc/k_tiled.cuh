@@ -1,0 +1,237 @@
+// Tiled dual-iteration kernel with temporal blocking (the hot loop of every ROF step).
+//
+// One CTA owns a tile of TH = RW*R rows by TW = 32*V columns, held entirely in registers:
+// lane l of warp wy owns columns [xs + lV, xs + lV + V) of rows [ys + wy R, ys + (wy+1) R).
+// The CTA loads p1, p2 and g/lambda of its tile once, runs up to TB Chambolle iterations in
+// registers, and stores the centre (the tile minus a halo of TB rows and roundup(TB, V)
+// columns on each side). One iteration at a pixel reads p at the offsets (0,0), (+-1,0),
+// (0,+-1), (+1,-1), (-1,+1), so after TB iterations exactly the centre is still exact; the
+// halo is recomputed by the neighbouring tiles (overlapped tiling).
+//
+// Neighbour exchange inside an iteration:
+//   - along a row (j +- 1): inside a lane's V columns in registers, across lanes by one warp
+//     shuffle per row;
+//   - along a column (i +- 1): inside a thread's R rows in registers, across warps through two
+//     shared-memory rows per warp (the bottom row of p1, the top row of w), with two CTA
+//     barriers per iteration.
+//
+// Image borders: pixels outside the image are loaded as zero and their gradient is masked to
+// zero, so p stays zero there; this realises p1_{-1,j} = p2_{i,-1} = 0. The gradient is also
+// masked on the last image row (G1) and column (G2): the Neumann boundary. Tiles that do not
+// touch a border skip all masks.
+#pragma once
+
+#include "chambolle_math.cuh"
+#include "tvspec_internal.h"
+
+namespace tvspec {
+
+template <typename P, int V>
+struct alignas(sizeof(P) * V) PPack {
+    P v[V];
+};
+template <int V>
+struct alignas(sizeof(float) * V) FPack {
+    float v[V];
+};
+
+template <int V, int R, int RW, bool FAST, bool EDGE>
+__device__ __forceinline__ void tiled_iterate(float (&p1)[R][V], float (&p2)[R][V],
+                                              const float (&gl)[R][V], int n_iter, float tau,
+                                              unsigned m1bits, unsigned m2bits,
+                                              float (*s_p1b)[32 * V], float (*s_wt)[32 * V],
+                                              int lane, int wy) {
+    constexpr unsigned FULL = 0xffffffffu;
+    float w[R][V];
+    for (int it = 0; it < n_iter; ++it) {
+        // ---- w = div p - g/lambda on every owned pixel
+        float up[V];
+        if (RW > 1 && wy > 0) {
+            FPack<V> q = *reinterpret_cast<const FPack<V> *>(&s_p1b[wy - 1][lane * V]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) up[v] = q.v[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) up[v] = 0.0f;  // tile top row: halo
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float left0 = __shfl_up_sync(FULL, p2[r][V - 1], 1);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float p1u = (r == 0) ? up[v] : p1[r - 1][v];
+                const float p2l = (v == 0) ? left0 : p2[r][v - 1];
+                w[r][v] = tv_w(p1[r][v], p1u, p2[r][v], p2l, gl[r][v]);
+            }
+        }
+        float dn[V];
+        if (RW > 1) {
+            FPack<V> q;
+#pragma unroll
+            for (int v = 0; v < V; ++v) q.v[v] = w[0][v];
+            *reinterpret_cast<FPack<V> *>(&s_wt[wy][lane * V]) = q;
+            __syncthreads();
+            if (wy < RW - 1) {
+                FPack<V> b = *reinterpret_cast<const FPack<V> *>(&s_wt[wy + 1][lane * V]);
+#pragma unroll
+                for (int v = 0; v < V; ++v) dn[v] = b.v[v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) dn[v] = w[R - 1][v];  // tile bottom row: halo
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) dn[v] = w[R - 1][v];
+        }
+        // ---- p <- (p + tau grad w) / (1 + tau |grad w|)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float right_last = __shfl_down_sync(FULL, w[r][0], 1);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float wd = (r < R - 1) ? w[r + 1][v] : dn[v];
+                const float wr = (v < V - 1) ? w[r][v + 1] : right_last;
+                float G1 = __fsub_rn(wd, w[r][v]);
+                float G2 = __fsub_rn(wr, w[r][v]);
+                if (EDGE) {
+                    G1 = ((m1bits >> (r * V + v)) & 1u) ? G1 : 0.0f;
+                    G2 = ((m2bits >> (r * V + v)) & 1u) ? G2 : 0.0f;
+                }
+                tv_update<FAST>(p1[r][v], p2[r][v], G1, G2, tau);
+            }
+        }
+        if (RW > 1) {
+            FPack<V> q;
+#pragma unroll
+            for (int v = 0; v < V; ++v) q.v[v] = p1[R - 1][v];
+            *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
+            __syncthreads();
+        }
+    }
+}
+
+template <int V, int R, int RW, int TB, typename P, bool FAST>
+__global__ void __launch_bounds__(32 * RW)
+    k_tiled(const TileRef *__restrict__ tiles, const ImgDesc *__restrict__ descs, int gstep,
+            int blk, int depth, float tau) {
+    static_assert(R * V <= 32, "mask bits");
+    constexpr int TW = 32 * V;
+    constexpr int TH = RW * R;
+    constexpr int HX = (TB + V - 1) / V * V;
+    constexpr int OW = TW - 2 * HX;
+    constexpr int OH = TH - 2 * TB;
+    static_assert(OW > 0 && OH > 0, "tile smaller than its halo");
+    __shared__ __align__(16) float s_p1b[RW][TW];
+    __shared__ __align__(16) float s_wt[RW][TW];
+
+    const TileRef t = tiles[blockIdx.x];
+    const ImgDesc *d = descs + t.img;
+    const int H = d->H, W = d->W, pitch = d->pitch;
+    // launch blk advances every tile by iterations [blk*depth, min((blk+1)*depth, n_inner));
+    // depth <= TB keeps the centre exact
+    const int k = gstep - d->s0;
+    const int n_iter = min(min(depth, TB), d->n_inner - blk * depth);
+    if (k < 0 || k >= d->K || n_iter <= 0) return;  // uniform over the CTA
+    const int src = p_copy(k, launches_per_step(d->n_inner, depth), blk);
+    const P *__restrict__ gp1 = static_cast<const P *>(d->p1[src]);
+    const P *__restrict__ gp2 = static_cast<const P *>(d->p2[src]);
+    P *__restrict__ op1 = static_cast<P *>(d->p1[src ^ 1]);
+    P *__restrict__ op2 = static_cast<P *>(d->p2[src ^ 1]);
+    const float *__restrict__ ggl = d->gl;
+
+    const int lane = threadIdx.x & 31;
+    const int wy = threadIdx.x >> 5;
+    const int x0 = t.tx * OW, y0 = t.ty * OH;
+    const int xs = x0 - HX, ys = y0 - TB;
+    const int cx = xs + lane * V;
+    const int ry = ys + wy * R;
+    const bool col_ok = (cx >= 0) && (cx < pitch);
+
+    float p1[R][V], p2[R][V], gl[R][V];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = ry + r;
+        if (col_ok && y >= 0 && y < H) {
+            const size_t off = (size_t)y * pitch + cx;
+            PPack<P, V> a = *reinterpret_cast<const PPack<P, V> *>(gp1 + off);
+            PPack<P, V> b = *reinterpret_cast<const PPack<P, V> *>(gp2 + off);
+            FPack<V> c = *reinterpret_cast<const FPack<V> *>(ggl + off);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                p1[r][v] = PStore<P>::load(a.v[v]);
+                p2[r][v] = PStore<P>::load(b.v[v]);
+                gl[r][v] = c.v[v];
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) p1[r][v] = p2[r][v] = gl[r][v] = 0.0f;
+        }
+    }
+    if (RW > 1) {
+        FPack<V> q;
+#pragma unroll
+        for (int v = 0; v < V; ++v) q.v[v] = p1[R - 1][v];
+        *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
+        __syncthreads();
+    }
+
+    const bool interior = ys >= 0 && ys + TH <= H - 1 && xs >= 0 && xs + TW <= W - 1;
+    if (interior) {
+        tiled_iterate<V, R, RW, FAST, false>(p1, p2, gl, n_iter, tau, 0u, 0u, s_p1b, s_wt, lane,
+                                             wy);
+    } else {
+        unsigned m1 = 0u, m2 = 0u;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = ry + r;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int c = cx + v;
+                const bool cin = c >= 0 && c < W;
+                if (y >= 0 && y < H - 1 && cin) m1 |= 1u << (r * V + v);
+                if (y >= 0 && y < H && c >= 0 && c < W - 1) m2 |= 1u << (r * V + v);
+            }
+        }
+        tiled_iterate<V, R, RW, FAST, true>(p1, p2, gl, n_iter, tau, m1, m2, s_p1b, s_wt, lane,
+                                            wy);
+    }
+
+    // store the exact centre into the other copy (the halo this CTA read belongs to other
+    // tiles' centres, which they write into that copy too, never into the one being read)
+    if (cx >= x0 && cx < x0 + OW && cx < W) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = ry + r;
+            if (y >= y0 && y < y0 + OH && y < H) {
+                const size_t off = (size_t)y * pitch + cx;
+                PPack<P, V> a, b;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    a.v[v] = PStore<P>::store(p1[r][v]);
+                    b.v[v] = PStore<P>::store(p2[r][v]);
+                }
+                *reinterpret_cast<PPack<P, V> *>(op1 + off) = a;
+                *reinterpret_cast<PPack<P, V> *>(op2 + off) = b;
+            }
+        }
+    }
+}
+
+// Shape list shared by every storage type; index = tile-shape id of the C ABI.
+#define TVSPEC_TILE_SHAPES(X) \
+    X(0, 4, 4, 16, 4)         \
+    X(1, 4, 4, 16, 8)         \
+    X(2, 4, 4, 8, 4)          \
+    X(3, 4, 4, 8, 8)          \
+    X(4, 2, 8, 8, 4)          \
+    X(5, 2, 8, 8, 8)          \
+    X(6, 2, 8, 16, 4)         \
+    X(7, 2, 8, 16, 8)         \
+    X(8, 2, 8, 4, 4)          \
+    X(9, 4, 4, 16, 12)        \
+    X(10, 2, 8, 16, 12)       \
+    X(11, 2, 4, 8, 2)
+
+using TiledKernel = void (*)(const TileRef *, const ImgDesc *, int, int, int, float);
+
+}  // namespace tvspec

@@ -1,0 +1,42 @@
+// Shape table and launcher of the tiled dual-iteration kernel.
+#include "k_tiled.cuh"
+
+namespace tvspec {
+
+TiledKernel tiled_kernel_f32(int shape, bool fast);
+TiledKernel tiled_kernel_f16(int shape, bool fast);
+TiledKernel tiled_kernel_bf16(int shape, bool fast);
+
+#define TVSPEC_SHAPE_ROW(idx, V, R, RW, TB) {V, R, RW, TB},
+static const TileShape kShapes[] = {TVSPEC_TILE_SHAPES(TVSPEC_SHAPE_ROW)};
+#undef TVSPEC_SHAPE_ROW
+
+int tiled_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
+
+TileShape tiled_shape(int index) { return kShapes[index]; }
+
+void tiled_output_tile(const TileShape &s, int *ow, int *oh) {
+    const int hx = (s.TB + s.V - 1) / s.V * s.V;
+    *ow = 32 * s.V - 2 * hx;
+    *oh = s.RW * s.R - 2 * s.TB;
+}
+
+cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *tiles, int n_tiles,
+                         const ImgDesc *descs, int gstep, int blk, int depth, float tau,
+                         cudaStream_t st) {
+    if (shape < 0 || shape >= tiled_shape_count()) return cudaErrorInvalidValue;
+    if (n_tiles <= 0) return cudaSuccess;
+    TiledKernel k = nullptr;
+    switch (p_storage) {
+        case 0: k = tiled_kernel_f32(shape, fast); break;
+        case 1: k = tiled_kernel_f16(shape, fast); break;
+        case 2: k = tiled_kernel_bf16(shape, fast); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (!k) return cudaErrorInvalidValue;
+    const int threads = 32 * kShapes[shape].RW;
+    k<<<n_tiles, threads, 0, st>>>(tiles, descs, gstep, blk, depth, tau);
+    return cudaGetLastError();
+}
+
+}  // namespace tvspec

@@ -1,0 +1,1016 @@
+// Host runtime: validation, device workspace, launch tables, autotuning, CUDA graphs and the
+// plain / batched entry points of the C ABI.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <sstream>
+
+#include "runtime.h"
+
+namespace tvspec {
+
+static thread_local std::string g_last_error;
+
+tvspec_status fail(tvspec_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+tvspec_status fail_cuda(cudaError_t e, const char *what) {
+    const tvspec_status s = (e == cudaErrorMemoryAllocation) ? TVSPEC_ENOMEM : TVSPEC_ECUDA;
+    return fail(s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+static int storage_bytes(int s) { return s == 0 ? 4 : 2; }
+static int pitch_for(int W) { return (W + 3) / 4 * 4; }
+static int ep_blocks_for(int H, int W) { return H * ((W + kEpBlock - 1) / kEpBlock); }
+
+// ---------------------------------------------------------------------------------------------
+// Validation. Band membership of t_k = k dt is decided here in float64 with the left-closed
+// reading of Eq. spectral_bands: band m collects the phi_k with e_m <= t_k < e_{m+1}.
+// ---------------------------------------------------------------------------------------------
+tvspec_status make_job(const tvspec_request &req, Job *out) {
+    if (req.H < 1 || req.W < 1) return fail(TVSPEC_EINVAL, "H and W must be >= 1");
+    if ((size_t)req.H * (size_t)req.W > ((size_t)1 << 28))
+        return fail(TVSPEC_EINVAL, "H*W exceeds 2^28");
+    if (!std::isfinite(req.dt) || !(req.dt > 0.0)) return fail(TVSPEC_EINVAL, "dt must be finite and > 0");
+    if (req.K < 2 || req.K > 100000) return fail(TVSPEC_EINVAL, "K must be in [2, 100000]");
+    if (req.n_inner < 0 || req.n_inner > 10000000)
+        return fail(TVSPEC_EINVAL, "n_inner must be in [0, 1e7]");
+    if (req.n_edges < 2 || req.n_edges > kMaxEdges)
+        return fail(TVSPEC_EINVAL, "n_edges must be in [2, 65]");
+    if (!req.band_edges) return fail(TVSPEC_EINVAL, "band_edges is NULL");
+    if (!req.f || !req.bands || !req.residual || !req.S)
+        return fail(TVSPEC_EINVAL, "f, bands, residual and S must be non-NULL");
+    if (req.mem_kind != TVSPEC_MEM_HOST && req.mem_kind != TVSPEC_MEM_DEVICE)
+        return fail(TVSPEC_EINVAL, "mem_kind must be TVSPEC_MEM_HOST or TVSPEC_MEM_DEVICE");
+    std::vector<double> e(req.band_edges, req.band_edges + req.n_edges);
+    if (std::isnan(e[0]) || !std::isfinite(e[0]) || e[0] < 0.0)
+        return fail(TVSPEC_EINVAL, "band_edges[0] must be finite and >= 0");
+    for (int m = 1; m < req.n_edges; ++m) {
+        if (std::isnan(e[m])) return fail(TVSPEC_EINVAL, "band edge is NaN");
+        if (!(e[m] > e[m - 1])) return fail(TVSPEC_EINVAL, "band edges must be strictly increasing");
+        if (!std::isfinite(e[m]) && m != req.n_edges - 1)
+            return fail(TVSPEC_EINVAL, "only the last band edge may be infinite");
+    }
+    if (req.mem_kind == TVSPEC_MEM_HOST) {
+        const size_t N = (size_t)req.H * (size_t)req.W;
+        for (size_t n = 0; n < N; ++n)
+            if (!std::isfinite(req.f[n])) return fail(TVSPEC_EINVAL, "f contains a non-finite value");
+    }
+    out->r = req;
+    out->edges = e;
+    out->band_of_k.assign(req.K, -1);
+    for (int k = 1; k < req.K; ++k) {
+        const double t = (double)k * req.dt;
+        for (int m = 0; m + 1 < req.n_edges; ++m)
+            if (e[m] <= t && t < e[m + 1]) {
+                out->band_of_k[k] = (signed char)m;
+                break;
+            }
+    }
+    out->r.band_edges = out->edges.data();
+    return TVSPEC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Workspace of one image. Layout of the single allocation:
+//   band_of_k | f | p1 p2 p1' p2' gl acc bands partials counter,status | ua ub residual S [trace]
+// The part from p1 to the status word is cleared at the start of every decomposition.
+// ---------------------------------------------------------------------------------------------
+struct SlotLayout {
+    size_t band, f, p1, p2, q1, q2, gl, acc, bands, partials, ctr, ua, ub, res, S, tr, zero_begin,
+        zero_end, total;
+};
+
+static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naive, bool trace) {
+    SlotLayout L{};
+    const size_t N = (size_t)H * W;
+    const int pitch = pitch_for(W);
+    const size_t pb = (size_t)H * pitch * storage_bytes(storage);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = a256(off + std::max<size_t>(bytes, 1));
+        return o;
+    };
+    L.band = take(K);
+    L.f = take(N * 4);
+    L.zero_begin = off;
+    L.p1 = take(pb);
+    L.p2 = take(pb);
+    L.q1 = take(pb);
+    L.q2 = take(pb);
+    L.gl = take((size_t)H * pitch * 4);
+    L.acc = take(N * 8);
+    L.bands = take((size_t)nb * N * 4);
+    L.partials = take((size_t)ep_blocks_for(H, W) * 8);
+    L.ctr = take(16);
+    L.zero_end = off;
+    L.ua = take(N * 8);
+    L.ub = take(N * 8);
+    L.res = take(N * 4);
+    L.S = take((size_t)std::max(K - 1, 1) * 8);
+    L.tr = trace ? take((size_t)(K + 1) * N * 8) : 0;
+    L.total = off;
+    return L;
+}
+
+size_t slot_bytes_for(const Job &j, int storage, bool naive) {
+    return layout_for(j.r.H, j.r.W, j.r.K, j.r.n_edges - 1, storage, naive, j.r.u_trace != nullptr)
+        .total;
+}
+
+tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStream_t st,
+                         bool async_alloc) {
+    const tvspec_request &r = j.r;
+    const bool trace = r.u_trace != nullptr;
+    const int nb = r.n_edges - 1;
+    const SlotLayout L = layout_for(r.H, r.W, r.K, nb, storage, naive, trace);
+    char *base = nullptr;
+    cudaError_t e = async_alloc ? cudaMallocAsync((void **)&base, L.total, st)
+                                : cudaMalloc((void **)&base, L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TVSPEC_ENOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
+    }
+    Slot x;
+    x.H = r.H;
+    x.W = r.W;
+    x.pitch = pitch_for(r.W);
+    x.K = r.K;
+    x.n_inner = r.n_inner;
+    x.n_bands = nb;
+    x.storage = storage;
+    x.trace = trace;
+    x.naive = naive;
+    x.async_alloc = async_alloc;
+    x.dt = r.dt;
+    x.base = base;
+    x.bytes = L.total;
+    x.zero_off = L.zero_begin;
+    x.zero_bytes = L.zero_end - L.zero_begin;
+    x.band_of_k = (signed char *)(base + L.band);
+    x.f = (float *)(base + L.f);
+    x.p1[0] = base + L.p1;
+    x.p2[0] = base + L.p2;
+    x.p1[1] = base + L.q1;
+    x.p2[1] = base + L.q2;
+    x.gl = (float *)(base + L.gl);
+    x.acc = (double *)(base + L.acc);
+    x.bands = (float *)(base + L.bands);
+    x.partials = (double *)(base + L.partials);
+    x.counter = (unsigned *)(base + L.ctr);
+    x.status = x.counter + 1;
+    x.ua = (double *)(base + L.ua);
+    x.ub = (double *)(base + L.ub);
+    x.residual = (float *)(base + L.res);
+    x.S = (double *)(base + L.S);
+    x.utrace = trace ? (double *)(base + L.tr) : nullptr;
+    x.ep_blocks = ep_blocks_for(r.H, r.W);
+    x.p_bytes = (size_t)r.H * x.pitch * storage_bytes(storage);
+    e = cudaMemcpyAsync(x.band_of_k, j.band_of_k.data(), r.K, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        if (async_alloc) cudaFreeAsync(base, st); else cudaFree(base);
+        return fail_cuda(e, "band table upload");
+    }
+    *s = x;
+    return TVSPEC_OK;
+}
+
+void slot_free(Slot *s, cudaStream_t st) {
+    if (s->base) {
+        if (s->async_alloc) cudaFreeAsync(s->base, st);
+        else cudaFree(s->base);
+    }
+    s->base = nullptr;
+}
+
+ImgDesc slot_desc(const Slot &s, int s0) {
+    ImgDesc d{};
+    d.f = s.f;
+    d.p1[0] = s.p1[0];
+    d.p1[1] = s.p1[1];
+    d.p2[0] = s.p2[0];
+    d.p2[1] = s.p2[1];
+    d.gl = s.gl;
+    d.ua = s.ua;
+    d.ub = s.ub;
+    d.acc = s.acc;
+    d.bands = s.bands;
+    d.residual = s.residual;
+    d.S = s.S;
+    d.u_trace = s.utrace;
+    d.partials = s.partials;
+    d.counter = s.counter;
+    d.status = s.status;
+    d.band_of_k = s.band_of_k;
+    d.H = s.H;
+    d.W = s.W;
+    d.pitch = s.pitch;
+    d.K = s.K;
+    d.n_inner = s.n_inner;
+    d.s0 = s0;
+    d.n_bands = s.n_bands;
+    d.ep_blocks = s.ep_blocks;
+    d.dt = s.dt;
+    d.inv_dt = 1.0 / s.dt;
+    return d;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launch tables.
+// ---------------------------------------------------------------------------------------------
+void LaunchSet::release() {
+    cudaFree(d_descs);
+    cudaFree(d_tiles);
+    cudaFree(d_ep_img);
+    cudaFree(d_ep_base);
+    d_descs = nullptr;
+    d_tiles = nullptr;
+    d_ep_img = d_ep_base = nullptr;
+    cap_descs = cap_tiles = cap_ep = 0;
+}
+
+void tiles_for(int shape, int H, int W, int *ntx, int *nty) {
+    int ow, oh;
+    tiled_output_tile(tiled_shape(shape), &ow, &oh);
+    *ntx = (W + ow - 1) / ow;
+    *nty = (H + oh - 1) / oh;
+}
+
+template <typename T>
+static tvspec_status grow_upload(T **dptr, size_t *cap, const std::vector<T> &h) {
+    const size_t need = std::max<size_t>(h.size(), 1);
+    if (need > *cap) {
+        cudaFree(*dptr);
+        *dptr = nullptr;
+        *cap = 0;
+        TV_CK(cudaMalloc((void **)dptr, need * sizeof(T)));
+        *cap = need;
+    }
+    if (!h.empty()) TV_CK(cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return TVSPEC_OK;
+}
+
+tvspec_status launchset_build(LaunchSet *ls, const std::vector<ImgDesc> &descs, int shape,
+                              int depth) {
+    const int n = (int)descs.size();
+    std::vector<TileRef> tiles;
+    std::vector<int> ep_img, ep_base(n);
+    ls->tile_prefix.assign(n + 1, 0);
+    ls->ep_prefix.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const ImgDesc &d = descs[i];
+        if (shape >= 0) {
+            int ntx, nty;
+            tiles_for(shape, d.H, d.W, &ntx, &nty);
+            for (int ty = 0; ty < nty; ++ty)
+                for (int tx = 0; tx < ntx; ++tx) tiles.push_back({i, tx, ty});
+        }
+        ls->tile_prefix[i + 1] = (int)tiles.size();
+        ep_base[i] = (int)ep_img.size();
+        for (int b = 0; b < d.ep_blocks; ++b) ep_img.push_back(i);
+        ls->ep_prefix[i + 1] = (int)ep_img.size();
+    }
+    tvspec_status s;
+    if ((s = grow_upload(&ls->d_descs, &ls->cap_descs, descs)) != TVSPEC_OK) return s;
+    if ((s = grow_upload(&ls->d_tiles, &ls->cap_tiles, tiles)) != TVSPEC_OK) return s;
+    if ((s = grow_upload(&ls->d_ep_img, &ls->cap_ep, ep_img)) != TVSPEC_OK) return s;
+    size_t cap_base = 0;
+    cudaFree(ls->d_ep_base);
+    ls->d_ep_base = nullptr;
+    if ((s = grow_upload(&ls->d_ep_base, &cap_base, ep_base)) != TVSPEC_OK) return s;
+    ls->n = n;
+    ls->shape = shape;
+    ls->depth = depth;
+    ls->h_descs = descs;
+    return TVSPEC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tile choice. Every shape gives bit-identical float32 results (the per-pixel arithmetic does
+// not depend on the tiling), so the autotuner may pick freely; with 16-bit storage of p the
+// rounding points depend on the iterations per launch, so there the depth is fixed.
+// ---------------------------------------------------------------------------------------------
+static int default_depth(const tvspec_config &c, int shape) {
+    const int TB = tiled_shape(shape).TB;
+    if (c.temporal_block > 0) return std::min(c.temporal_block, TB);
+    if (c.p_storage != TVSPEC_P_FP32) return std::min(8, TB);
+    return TB;
+}
+
+tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, cudaStream_t st,
+                           int *shape, int *depth) {
+    const tvspec_config &c = plan->cfg;
+    if (c.kernel == TVSPEC_KERNEL_NAIVE) {
+        *shape = -1;
+        *depth = 1;
+        return TVSPEC_OK;
+    }
+    std::vector<int> cands;
+    if (c.tile >= 0) {
+        cands.push_back(c.tile);
+    } else {
+        for (int s = 0; s < tiled_shape_count(); ++s) {
+            if (c.p_storage != TVSPEC_P_FP32 && c.temporal_block == 0 && tiled_shape(s).TB < 8)
+                continue;
+            cands.push_back(s);
+        }
+    }
+    if (cands.size() == 1) {
+        *shape = cands[0];
+        *depth = default_depth(c, cands[0]);
+        return TVSPEC_OK;
+    }
+    std::vector<std::pair<int, int>> dims;
+    for (Slot *s : slots) dims.push_back({s->H, s->W});
+    std::sort(dims.begin(), dims.end());
+    std::ostringstream key;
+    key << c.p_storage << '/' << c.fast_math << '/' << c.temporal_block;
+    for (auto &d : dims) key << ';' << d.first << 'x' << d.second;
+    auto it = plan->tune.find(key.str());
+    if (it != plan->tune.end()) {
+        *shape = it->second.first;
+        *depth = it->second.second;
+        return TVSPEC_OK;
+    }
+    double total_px = 0.0;
+    for (Slot *s : slots) total_px += (double)s->H * s->W;
+    cudaEvent_t e0, e1;
+    TV_CK(cudaEventCreate(&e0));
+    TV_CK(cudaEventCreate(&e1));
+    int best = cands[0], best_depth = default_depth(c, cands[0]);
+    double best_cost = 1e300;
+    for (int cand : cands) {
+        const int dep = default_depth(c, cand);
+        std::vector<ImgDesc> descs;
+        for (Slot *s : slots) {
+            ImgDesc d = slot_desc(*s, 0);
+            d.n_inner = dep;  // every tile runs exactly `dep` iterations in launch 0
+            descs.push_back(d);
+        }
+        LaunchSet ls;
+        tvspec_status s = launchset_build(&ls, descs, cand, dep);
+        if (s != TVSPEC_OK) {
+            ls.release();
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return s;
+        }
+        const int nt = ls.tile_prefix[ls.n];
+        cudaError_t e = launch_tiled(cand, c.p_storage, c.fast_math != 0, ls.d_tiles, nt,
+                                     ls.d_descs, 0, 0, dep, c.tau, st);
+        const int reps = 3;
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = launch_tiled(cand, c.p_storage, c.fast_math != 0, ls.d_tiles, nt, ls.d_descs, 0,
+                             0, dep, c.tau, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        ls.release();
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail_cuda(e, "autotune launch");
+        }
+        const double cost = (double)ms / (reps * dep * total_px);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = cand;
+            best_depth = dep;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan->tune[key.str()] = {best, best_depth};
+    *shape = best;
+    *depth = best_depth;
+    return TVSPEC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device work of one ROF step.
+// ---------------------------------------------------------------------------------------------
+static tvspec_status enqueue_iterations(tvspec_plan *plan, LaunchSet &ls,
+                                        std::vector<Slot *> &slots, int n_active, int gstep,
+                                        cudaStream_t st, uint64_t *nk) {
+    const tvspec_config &c = plan->cfg;
+    if (ls.shape < 0) {
+        // reference kernel: single image, one launch per iteration between the two copies
+        Slot &s = *slots[0];
+        const ImgDesc &d = ls.h_descs[0];
+        const int k = gstep - d.s0;
+        if (k < 0 || k >= d.K) return TVSPEC_OK;
+        const int n_it = d.n_inner;
+        for (int it = 0; it < n_it; ++it) {
+            const int src = p_copy(k, n_it, it);
+            cudaError_t e = launch_naive(c.p_storage, c.fast_math != 0, d.p1[src], d.p2[src],
+                                         d.p1[src ^ 1], d.p2[src ^ 1], s.gl, s.H, s.W, s.pitch,
+                                         c.tau, st);
+            if (e != cudaSuccess) return fail_cuda(e, "reference kernel launch");
+            ++*nk;
+        }
+        return TVSPEC_OK;
+    }
+    int nblk = 0;
+    for (int i = 0; i < n_active; ++i) {
+        const ImgDesc &d = ls.h_descs[i];
+        const int k = gstep - d.s0;
+        if (k < 0 || k >= d.K) continue;
+        nblk = std::max(nblk, launches_per_step(d.n_inner, ls.depth));
+    }
+    const int nt = ls.tile_prefix[n_active];
+    for (int b = 0; b < nblk; ++b) {
+        cudaError_t e = launch_tiled(ls.shape, c.p_storage, c.fast_math != 0, ls.d_tiles, nt,
+                                     ls.d_descs, gstep, b, ls.depth, c.tau, st);
+        if (e != cudaSuccess) return fail_cuda(e, "tiled kernel launch");
+        ++*nk;
+    }
+    return TVSPEC_OK;
+}
+
+tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *> &slots,
+                           int n_active, int gstep, cudaStream_t st, uint64_t *nk) {
+    const tvspec_config &c = plan->cfg;
+    if (!c.warm_start) {
+        for (int i = 0; i < n_active; ++i) {
+            const int k = gstep - ls.h_descs[i].s0;
+            if (k < 0 || k >= slots[i]->K) continue;
+            for (int cpy = 0; cpy < 2; ++cpy) {
+                TV_CK(cudaMemsetAsync(slots[i]->p1[cpy], 0, slots[i]->p_bytes, st));
+                TV_CK(cudaMemsetAsync(slots[i]->p2[cpy], 0, slots[i]->p_bytes, st));
+            }
+        }
+    }
+    tvspec_status s = enqueue_iterations(plan, ls, slots, n_active, gstep, st, nk);
+    if (s != TVSPEC_OK) return s;
+    cudaError_t e = launch_epilogue(c.p_storage, ls.d_descs, ls.d_ep_img, ls.d_ep_base,
+                                    ls.ep_prefix[n_active], gstep, ls.shape < 0 ? 1 : ls.depth, st);
+    if (e != cudaSuccess) return fail_cuda(e, "epilogue launch");
+    if (ls.ep_prefix[n_active] > 0) ++*nk;
+    return TVSPEC_OK;
+}
+
+// The whole decomposition of a cached batch, from cleared workspace to the last epilogue.
+static tvspec_status enqueue_decomposition(tvspec_plan *plan, CacheEntry &E, cudaStream_t st,
+                                           uint64_t *nk) {
+    std::vector<Slot *> sp;
+    for (Slot &s : E.slots) sp.push_back(&s);
+    for (Slot &s : E.slots) TV_CK(cudaMemsetAsync(s.base + s.zero_off, 0, s.zero_bytes, st));
+    cudaError_t e = launch_init(E.ls.d_descs, E.ls.d_ep_img, E.ls.d_ep_base,
+                                E.ls.ep_prefix[E.ls.n], st);
+    if (e != cudaSuccess) return fail_cuda(e, "init launch");
+    ++*nk;
+    for (int g = 0; g < E.maxK; ++g) {
+        int n_active = 0;
+        while (n_active < (int)E.slots.size() && E.slots[n_active].K > g) ++n_active;
+        tvspec_status s = enqueue_step(plan, E.ls, sp, n_active, g, st, nk);
+        if (s != TVSPEC_OK) return s;
+    }
+    return TVSPEC_OK;
+}
+
+static void free_entry(CacheEntry &E, cudaStream_t st) {
+    if (E.exec) cudaGraphExecDestroy(E.exec);
+    if (E.graph) cudaGraphDestroy(E.graph);
+    E.exec = nullptr;
+    E.graph = nullptr;
+    for (Slot &s : E.slots) slot_free(&s, st);
+    E.slots.clear();
+    E.ls.release();
+    if (E.h_status) cudaFreeHost(E.h_status);
+    E.h_status = nullptr;
+}
+
+static std::string job_key(const tvspec_config &c, const std::vector<Job> &jobs) {
+    std::ostringstream k;
+    k << c.p_storage << '/' << c.warm_start << '/' << c.tau << '/' << c.kernel << '/' << c.tile
+      << '/' << c.temporal_block << '/' << c.fast_math << '/' << c.use_graphs;
+    k.precision(17);
+    for (const Job &j : jobs) {
+        k << ';' << j.r.H << 'x' << j.r.W << ',' << j.r.K << ',' << j.r.n_inner << ',' << j.r.dt
+          << ',' << (j.r.u_trace ? 1 : 0);
+        for (double e : j.edges) k << ',' << e;
+    }
+    return k.str();
+}
+
+static tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs,
+                               CacheEntry **out) {
+    const std::string key = job_key(plan->cfg, jobs);
+    for (auto it = plan->cache.begin(); it != plan->cache.end(); ++it) {
+        if ((*it)->key == key) {
+            plan->cache.splice(plan->cache.begin(), plan->cache, it);
+            *out = plan->cache.front().get();
+            return TVSPEC_OK;
+        }
+    }
+    // new entry: workspace, tile choice, tables, optionally a captured graph
+    TV_CK(cudaStreamSynchronize(plan->stream));
+    while (plan->cache.size() >= 4) {
+        free_entry(*plan->cache.back(), plan->stream);
+        plan->cache.pop_back();
+    }
+    auto E = std::make_unique<CacheEntry>();
+    E->key = key;
+    const int n = (int)jobs.size();
+    E->order.resize(n);
+    for (int i = 0; i < n; ++i) E->order[i] = i;
+    std::stable_sort(E->order.begin(), E->order.end(),
+                     [&](int a, int b) { return jobs[a].r.K > jobs[b].r.K; });
+    const bool naive = plan->cfg.kernel == TVSPEC_KERNEL_NAIVE;
+    if (naive && n != 1) return fail(TVSPEC_ENOTSUP, "the reference kernel runs one image at a time");
+    for (int i = 0; i < n; ++i) {
+        Slot s;
+        tvspec_status st = slot_alloc(&s, jobs[E->order[i]], plan->cfg.p_storage, naive,
+                                      plan->stream, false);
+        if (st != TVSPEC_OK) {
+            free_entry(*E, plan->stream);
+            return st;
+        }
+        E->slots.push_back(s);
+        E->maxK = std::max(E->maxK, s.K);
+    }
+    TV_CK(cudaStreamSynchronize(plan->stream));
+    std::vector<Slot *> sp;
+    for (Slot &s : E->slots) sp.push_back(&s);
+    int shape = -1, depth = 1;
+    tvspec_status st = choose_tiles(plan, sp, plan->stream, &shape, &depth);
+    if (st != TVSPEC_OK) {
+        free_entry(*E, plan->stream);
+        return st;
+    }
+    std::vector<ImgDesc> descs;
+    for (Slot &s : E->slots) descs.push_back(slot_desc(s, 0));
+    st = launchset_build(&E->ls, descs, shape, depth);
+    if (st != TVSPEC_OK) {
+        free_entry(*E, plan->stream);
+        return st;
+    }
+    if (cudaMallocHost((void **)&E->h_status, sizeof(unsigned) * n) != cudaSuccess) {
+        free_entry(*E, plan->stream);
+        return fail(TVSPEC_ENOMEM, "pinned status words");
+    }
+    if (plan->cfg.use_graphs) {
+        uint64_t nk = 0;
+        TV_CK(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
+        st = enqueue_decomposition(plan, *E, plan->stream, &nk);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(plan->stream, &g);
+        if (st != TVSPEC_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            free_entry(*E, plan->stream);
+            return st != TVSPEC_OK ? st : fail_cuda(e, "graph capture");
+        }
+        E->graph = g;
+        e = cudaGraphInstantiate(&E->exec, g, 0);
+        if (e != cudaSuccess) {
+            free_entry(*E, plan->stream);
+            return fail_cuda(e, "graph instantiation");
+        }
+        E->graph_kernels = nk;
+        plan->graphs_built++;
+    }
+    plan->last_tile = shape;
+    plan->last_depth = depth;
+    plan->cache.push_front(std::move(E));
+    *out = plan->cache.front().get();
+    return TVSPEC_OK;
+}
+
+static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStream_t user_st) {
+    std::lock_guard<std::mutex> lock(plan->mu);
+    TV_CK(cudaSetDevice(plan->device));
+    const int mk = jobs[0].r.mem_kind;
+    for (const Job &j : jobs)
+        if (j.r.mem_kind != mk) return fail(TVSPEC_EINVAL, "all requests must share one mem_kind");
+    CacheEntry *E = nullptr;
+    tvspec_status s = get_entry(plan, jobs, &E);
+    if (s != TVSPEC_OK) return s;
+    cudaStream_t st = user_st ? user_st : plan->stream;
+    if (user_st) {
+        // order the (possibly different) user stream after anything still on the plan stream
+        cudaEvent_t ev;
+        TV_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        TV_CK(cudaEventRecord(ev, plan->stream));
+        TV_CK(cudaStreamWaitEvent(st, ev, 0));
+        cudaEventDestroy(ev);
+    }
+    const cudaMemcpyKind in_kind = mk == TVSPEC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind out_kind = mk == TVSPEC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int n = (int)jobs.size();
+    for (int i = 0; i < n; ++i) {
+        const tvspec_request &r = jobs[E->order[i]].r;
+        TV_CK(cudaMemcpyAsync(E->slots[i].f, r.f, (size_t)r.H * r.W * 4, in_kind, st));
+    }
+    uint64_t nk = 0;
+    if (E->exec) {
+        TV_CK(cudaGraphLaunch(E->exec, st));
+        nk = E->graph_kernels;
+        plan->graph_launches++;
+    } else {
+        s = enqueue_decomposition(plan, *E, st, &nk);
+        if (s != TVSPEC_OK) return s;
+    }
+    plan->kernel_launches += nk;
+    for (int i = 0; i < n; ++i) {
+        const tvspec_request &r = jobs[E->order[i]].r;
+        const Slot &sl = E->slots[i];
+        const size_t N = (size_t)r.H * r.W;
+        TV_CK(cudaMemcpyAsync(r.bands, sl.bands, (size_t)sl.n_bands * N * 4, out_kind, st));
+        TV_CK(cudaMemcpyAsync(r.residual, sl.residual, N * 4, out_kind, st));
+        TV_CK(cudaMemcpyAsync(r.S, sl.S, (size_t)(r.K - 1) * 8, out_kind, st));
+        if (r.u_trace)
+            TV_CK(cudaMemcpyAsync(r.u_trace, sl.utrace, (size_t)(r.K + 1) * N * 8, out_kind, st));
+        TV_CK(cudaMemcpyAsync(E->h_status + i, sl.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    }
+    if (user_st) {
+        // later work on the plan stream must see this call's use of the workspace
+        cudaEvent_t ev;
+        TV_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        TV_CK(cudaEventRecord(ev, st));
+        TV_CK(cudaStreamWaitEvent(plan->stream, ev, 0));
+        cudaEventDestroy(ev);
+    }
+    if (mk == TVSPEC_MEM_HOST) {
+        TV_CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i)
+            if (E->h_status[i] & kStatusNonFinite)
+                return fail(TVSPEC_ECUDA, "non-finite value in the flow");
+    }
+    plan->decompositions += n;
+    return TVSPEC_OK;
+}
+
+size_t plan_budget(const tvspec_plan *plan) {
+    return plan->cfg.mem_budget_bytes ? plan->cfg.mem_budget_bytes : ((size_t)60 << 30);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Standalone dual iterations (ROF step, hot-kernel timing).
+// ---------------------------------------------------------------------------------------------
+static tvspec_status scratch_slot(tvspec_plan *plan, int H, int W, Slot **out) {
+    for (Slot &s : plan->scratch)
+        if (s.H == H && s.W == W) {
+            *out = &s;
+            return TVSPEC_OK;
+        }
+    if (plan->scratch.size() >= 4) {
+        TV_CK(cudaStreamSynchronize(plan->stream));
+        slot_free(&plan->scratch.front(), plan->stream);
+        plan->scratch.pop_front();
+    }
+    const double edges[2] = {0.0, INFINITY};
+    tvspec_request r{};
+    r.H = H;
+    r.W = W;
+    r.dt = 1.0;
+    r.K = 2;
+    r.n_inner = 0;
+    r.n_edges = 2;
+    r.band_edges = edges;
+    Job j;
+    j.r = r;
+    j.edges.assign(edges, edges + 2);
+    j.band_of_k.assign(2, -1);
+    Slot s;
+    tvspec_status st = slot_alloc(&s, j, plan->cfg.p_storage, true, plan->stream, false);
+    if (st != TVSPEC_OK) return st;
+    TV_CK(cudaMemsetAsync(s.base + s.zero_off, 0, s.zero_bytes, plan->stream));
+    plan->scratch.push_back(s);
+    *out = &plan->scratch.back();
+    return TVSPEC_OK;
+}
+
+// Runs d.n_inner dual iterations as local step 0 of the image described by d (two copies of
+// p, copy 0 holding the start); *final_copy receives the copy holding the result.
+static tvspec_status run_iterations(tvspec_plan *plan, ImgDesc d, cudaStream_t st,
+                                    int *final_copy) {
+    Slot *tune_slot = nullptr;
+    tvspec_status s = scratch_slot(plan, d.H, d.W, &tune_slot);
+    if (s != TVSPEC_OK) return s;
+    int shape = -1, depth = 1;
+    std::vector<Slot *> sp{tune_slot};
+    s = choose_tiles(plan, sp, plan->stream, &shape, &depth);
+    if (s != TVSPEC_OK) return s;
+    d.s0 = 0;
+    d.K = std::max(d.K, 1);
+    std::ostringstream key;
+    key << d.p1[0] << '/' << d.p1[1] << '/' << d.p2[0] << '/' << d.p2[1] << '/' << d.gl << '/'
+        << d.H << 'x' << d.W << '/' << d.pitch << '/' << d.n_inner << '/' << shape << '/' << depth;
+    auto it = plan->iter_sets.find(key.str());
+    LaunchSet *ls = nullptr;
+    if (it == plan->iter_sets.end()) {
+        if (plan->iter_sets.size() >= 16) {
+            TV_CK(cudaDeviceSynchronize());
+            for (auto &kv : plan->iter_sets) kv.second->release();
+            plan->iter_sets.clear();
+        }
+        auto nls = std::make_unique<LaunchSet>();
+        s = launchset_build(nls.get(), std::vector<ImgDesc>{d}, shape, depth);
+        if (s != TVSPEC_OK) {
+            nls->release();
+            return s;
+        }
+        ls = nls.get();
+        plan->iter_sets[key.str()] = std::move(nls);
+    } else {
+        ls = it->second.get();
+    }
+    uint64_t nk = 0;
+    Slot tmp;
+    tmp.H = d.H;
+    tmp.W = d.W;
+    tmp.pitch = d.pitch;
+    tmp.K = d.K;
+    tmp.gl = d.gl;
+    std::vector<Slot *> one{&tmp};
+    s = enqueue_iterations(plan, *ls, one, 1, 0, st, &nk);
+    plan->kernel_launches += nk;
+    plan->last_tile = shape;
+    plan->last_depth = depth;
+    *final_copy = p_copy(1, shape < 0 ? d.n_inner : launches_per_step(d.n_inner, depth), 0);
+    return s;
+}
+
+}  // namespace tvspec
+
+using namespace tvspec;
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+void tvspec_config_init(tvspec_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->p_storage = TVSPEC_P_FP32;
+    cfg->warm_start = 1;
+    cfg->tau = 0.125f;
+    cfg->kernel = TVSPEC_KERNEL_AUTO;
+    cfg->tile = -1;
+    cfg->temporal_block = 0;
+    cfg->use_graphs = 1;
+    cfg->fast_math = 1;
+    cfg->mem_budget_bytes = 0;
+    cfg->max_batch = 0;
+}
+
+tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_plan **out) {
+    if (!out) return fail(TVSPEC_EINVAL, "out is NULL");
+    *out = nullptr;
+    tvspec_config c;
+    if (cfg) c = *cfg; else tvspec_config_init(&c);
+    if (c.p_storage < 0 || c.p_storage > 2) return fail(TVSPEC_EINVAL, "p_storage out of range");
+    if (!(c.tau > 0.0f) || !(c.tau <= 0.25f)) return fail(TVSPEC_EINVAL, "tau must be in (0, 0.25]");
+    if (c.kernel < 0 || c.kernel > 2) return fail(TVSPEC_EINVAL, "kernel out of range");
+    if (c.tile < -1 || c.tile >= tiled_shape_count()) return fail(TVSPEC_EINVAL, "tile out of range");
+    if (c.temporal_block < 0 || c.temporal_block > 16)
+        return fail(TVSPEC_EINVAL, "temporal_block must be in [0, 16]");
+    if (c.max_batch < 0) return fail(TVSPEC_EINVAL, "max_batch must be >= 0");
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess || n_dev == 0) {
+        cudaGetLastError();
+        return fail(TVSPEC_ECUDA, "no CUDA device available");
+    }
+    if (device < 0 || device >= n_dev) return fail(TVSPEC_EINVAL, "device index out of range");
+    TV_CK(cudaSetDevice(device));
+    auto *p = new (std::nothrow) tvspec_plan();
+    if (!p) return fail(TVSPEC_ENOMEM, "plan allocation");
+    p->device = device;
+    p->cfg = c;
+    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete p;
+        return fail_cuda(e, "stream creation");
+    }
+    *out = p;
+    return TVSPEC_OK;
+}
+
+// serving.cu
+void tvspec_server_stop(tvspec_plan *plan);
+
+tvspec_status tvspec_plan_destroy(tvspec_plan *plan) {
+    if (!plan) return TVSPEC_OK;
+    tvspec_server_stop(plan);
+    cudaSetDevice(plan->device);
+    cudaStreamSynchronize(plan->stream);
+    for (auto &E : plan->cache) free_entry(*E, plan->stream);
+    plan->cache.clear();
+    for (auto &kv : plan->iter_sets) kv.second->release();
+    plan->iter_sets.clear();
+    for (Slot &s : plan->scratch) slot_free(&s, plan->stream);
+    plan->scratch.clear();
+    cudaFree(plan->ping);
+    plan->ping = nullptr;
+    cudaStreamSynchronize(plan->stream);
+    cudaStreamDestroy(plan->stream);
+    delete plan;
+    return TVSPEC_OK;
+}
+
+tvspec_status tvspec_validate(const tvspec_request *req) {
+    if (!req) return fail(TVSPEC_EINVAL, "request is NULL");
+    Job j;
+    return make_job(*req, &j);
+}
+
+tvspec_status tvspec_decompose_ex(tvspec_plan *plan, const tvspec_request *req, void *stream) {
+    if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
+    if (!req) return fail(TVSPEC_EINVAL, "request is NULL");
+    std::vector<Job> jobs(1);
+    tvspec_status s = make_job(*req, &jobs[0]);
+    if (s != TVSPEC_OK) return s;
+    return run_jobs(plan, jobs, (cudaStream_t)stream);
+}
+
+tvspec_status tvspec_decompose(tvspec_plan *plan, const float *f, int H, int W, double dt, int K,
+                               int n_inner, const double *band_edges, int n_edges, float *bands,
+                               float *residual, double *S, int mem_kind, void *stream) {
+    tvspec_request r{};
+    r.f = f;
+    r.H = H;
+    r.W = W;
+    r.dt = dt;
+    r.K = K;
+    r.n_inner = n_inner;
+    r.band_edges = band_edges;
+    r.n_edges = n_edges;
+    r.bands = bands;
+    r.residual = residual;
+    r.S = S;
+    r.u_trace = nullptr;
+    r.mem_kind = mem_kind;
+    return tvspec_decompose_ex(plan, &r, stream);
+}
+
+tvspec_status tvspec_decompose_batch(tvspec_plan *plan, int n, const tvspec_request *reqs,
+                                     void *stream) {
+    if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
+    if (n < 1 || !reqs) return fail(TVSPEC_EINVAL, "need n >= 1 requests");
+    if (n > 4096) return fail(TVSPEC_EINVAL, "at most 4096 requests per batch");
+    std::vector<Job> jobs(n);
+    for (int i = 0; i < n; ++i) {
+        tvspec_status s = make_job(reqs[i], &jobs[i]);
+        if (s != TVSPEC_OK) return s;
+    }
+    return run_jobs(plan, jobs, (cudaStream_t)stream);
+}
+
+tvspec_status tvspec_rof_step(tvspec_plan *plan, const float *g, int H, int W, double lambda,
+                              int n_iter, float *p1, float *p2, float *u, int mem_kind,
+                              void *stream) {
+    if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
+    if (!g || !p1 || !p2 || !u) return fail(TVSPEC_EINVAL, "NULL buffer");
+    if (H < 1 || W < 1 || (size_t)H * W > ((size_t)1 << 28)) return fail(TVSPEC_EINVAL, "bad H, W");
+    if (!std::isfinite(lambda) || !(lambda > 0.0)) return fail(TVSPEC_EINVAL, "lambda must be > 0");
+    if (n_iter < 0 || n_iter > 10000000) return fail(TVSPEC_EINVAL, "n_iter out of range");
+    if (mem_kind != TVSPEC_MEM_HOST && mem_kind != TVSPEC_MEM_DEVICE)
+        return fail(TVSPEC_EINVAL, "bad mem_kind");
+    if (plan->cfg.p_storage != TVSPEC_P_FP32)
+        return fail(TVSPEC_ENOTSUP, "tvspec_rof_step needs p_storage = fp32");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    TV_CK(cudaSetDevice(plan->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : plan->stream;
+    if (stream) TV_CK(cudaStreamSynchronize(plan->stream));
+    Slot *sl = nullptr;
+    tvspec_status s = scratch_slot(plan, H, W, &sl);
+    if (s != TVSPEC_OK) return s;
+    {
+        // tune first: the autotuner times kernels on these very buffers
+        int shape, depth;
+        std::vector<Slot *> sp{sl};
+        s = choose_tiles(plan, sp, plan->stream, &shape, &depth);
+        if (s != TVSPEC_OK) return s;
+        TV_CK(cudaStreamSynchronize(plan->stream));
+    }
+    const cudaMemcpyKind in_kind = mem_kind == TVSPEC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind out_kind = mem_kind == TVSPEC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    TV_CK(cudaMemsetAsync(sl->base + sl->zero_off, 0, sl->zero_bytes, st));
+    const size_t row = (size_t)W * 4, prow = (size_t)sl->pitch * 4;
+    TV_CK(cudaMemcpy2DAsync(sl->p1[0], prow, p1, row, row, H, in_kind, st));
+    TV_CK(cudaMemcpy2DAsync(sl->p2[0], prow, p2, row, row, H, in_kind, st));
+    TV_CK(cudaMemcpyAsync(sl->f, g, (size_t)H * W * 4, in_kind, st));
+    cudaError_t e = launch_gl_from_g(sl->f, sl->gl, H, W, sl->pitch, lambda, st);
+    if (e != cudaSuccess) return fail_cuda(e, "gl kernel");
+    ImgDesc d = slot_desc(*sl, 0);
+    d.n_inner = n_iter;
+    int fc = 0;
+    s = run_iterations(plan, d, st, &fc);
+    if (s != TVSPEC_OK) return s;
+    e = launch_rof_primal((const float *)sl->p1[fc], (const float *)sl->p2[fc], sl->pitch, sl->f,
+                          sl->residual, H, W, lambda, st);
+    if (e != cudaSuccess) return fail_cuda(e, "primal kernel");
+    TV_CK(cudaMemcpy2DAsync(p1, row, sl->p1[fc], prow, row, H, out_kind, st));
+    TV_CK(cudaMemcpy2DAsync(p2, row, sl->p2[fc], prow, row, H, out_kind, st));
+    TV_CK(cudaMemcpyAsync(u, sl->residual, (size_t)H * W * 4, out_kind, st));
+    TV_CK(cudaStreamSynchronize(st));
+    return TVSPEC_OK;
+}
+
+tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float *p1, float *p2,
+                                       int H, int W, int pitch, int n_iter, void *stream) {
+    if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
+    if (!gl || !p1 || !p2) return fail(TVSPEC_EINVAL, "NULL buffer");
+    if (H < 1 || W < 1 || pitch < W || pitch % 4 != 0) return fail(TVSPEC_EINVAL, "bad H, W or pitch");
+    if (((uintptr_t)gl | (uintptr_t)p1 | (uintptr_t)p2) & 15u)
+        return fail(TVSPEC_EINVAL, "buffers must be 16-byte aligned");
+    if (n_iter < 0) return fail(TVSPEC_EINVAL, "n_iter < 0");
+    if (plan->cfg.p_storage != TVSPEC_P_FP32)
+        return fail(TVSPEC_ENOTSUP, "tvspec_chambolle_iterate needs p_storage = fp32");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    TV_CK(cudaSetDevice(plan->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : plan->stream;
+    // copy 1 of the dual field: a plan-owned buffer of the caller's pitched size
+    const size_t pb = (size_t)H * pitch * 4;
+    if (plan->ping_bytes < 2 * pb) {
+        TV_CK(cudaStreamSynchronize(st));
+        cudaFree(plan->ping);
+        plan->ping = nullptr;
+        plan->ping_bytes = 0;
+        TV_CK(cudaMalloc(&plan->ping, 2 * pb));
+        plan->ping_bytes = 2 * pb;
+    }
+    ImgDesc d{};
+    d.p1[0] = p1;
+    d.p2[0] = p2;
+    d.p1[1] = plan->ping;
+    d.p2[1] = (char *)plan->ping + pb;
+    d.gl = const_cast<float *>(gl);
+    d.H = H;
+    d.W = W;
+    d.pitch = pitch;
+    d.K = 1;
+    d.n_inner = n_iter;
+    d.s0 = 0;
+    d.dt = 1.0;
+    d.inv_dt = 1.0;
+    int fc = 0;
+    tvspec_status s = run_iterations(plan, d, st, &fc);
+    if (s != TVSPEC_OK) return s;
+    if (fc == 1) {
+        TV_CK(cudaMemcpyAsync(p1, d.p1[1], pb, cudaMemcpyDeviceToDevice, st));
+        TV_CK(cudaMemcpyAsync(p2, d.p2[1], pb, cudaMemcpyDeviceToDevice, st));
+    }
+    return TVSPEC_OK;
+}
+
+int tvspec_tile_count(void) { return tiled_shape_count(); }
+
+tvspec_status tvspec_tile_info(int index, int *cols_per_lane, int *rows_per_thread, int *warps,
+                               int *max_temporal_block) {
+    if (index < 0 || index >= tiled_shape_count()) return fail(TVSPEC_EINVAL, "tile index out of range");
+    const TileShape s = tiled_shape(index);
+    if (cols_per_lane) *cols_per_lane = s.V;
+    if (rows_per_thread) *rows_per_thread = s.R;
+    if (warps) *warps = s.RW;
+    if (max_temporal_block) *max_temporal_block = s.TB;
+    return TVSPEC_OK;
+}
+
+tvspec_status tvspec_plan_stats(tvspec_plan *plan, tvspec_stats *out) {
+    if (!plan || !out) return fail(TVSPEC_EINVAL, "NULL argument");
+    out->kernel_launches = plan->kernel_launches.load();
+    out->graph_launches = plan->graph_launches.load();
+    out->graphs_built = plan->graphs_built.load();
+    out->decompositions = plan->decompositions.load();
+    size_t ws = 0;
+    {
+        std::lock_guard<std::mutex> lock(plan->mu);
+        for (auto &E : plan->cache)
+            for (auto &s : E->slots) ws += s.bytes;
+        for (auto &s : plan->scratch) ws += s.bytes;
+    }
+    out->workspace_bytes = ws;
+    out->last_tile = plan->last_tile.load();
+    out->last_temporal_block = plan->last_depth.load();
+    return TVSPEC_OK;
+}
+
+const char *tvspec_status_str(tvspec_status status) {
+    switch (status) {
+        case TVSPEC_OK: return "TVSPEC_OK";
+        case TVSPEC_EINVAL: return "TVSPEC_EINVAL";
+        case TVSPEC_ENOMEM: return "TVSPEC_ENOMEM";
+        case TVSPEC_ECUDA: return "TVSPEC_ECUDA";
+        case TVSPEC_ETIMEOUT: return "TVSPEC_ETIMEOUT";
+        case TVSPEC_ENOTREADY: return "TVSPEC_ENOTREADY";
+        case TVSPEC_ECANCELLED: return "TVSPEC_ECANCELLED";
+        case TVSPEC_ENOTSUP: return "TVSPEC_ENOTSUP";
+        default: return "TVSPEC_UNKNOWN";
+    }
+}
+
+const char *tvspec_last_error(void) { return g_last_error.c_str(); }
+
+const char *tvspec_version(void) { return "tvspec 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Host runtime shared by the plain, batched and served paths.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "tvspec.h"
+#include "tvspec_internal.h"
+
+namespace tvspec {
+
+// Records msg as the thread's last error and returns s.
+tvspec_status fail(tvspec_status s, const std::string &msg);
+tvspec_status fail_cuda(cudaError_t e, const char *what);
+
+#define TV_CK(call)                                               \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ::tvspec::fail_cuda(e_, #call); \
+    } while (0)
+
+// A validated request plus what the host derives from it in float64.
+struct Job {
+    tvspec_request r;
+    std::vector<double> edges;
+    std::vector<signed char> band_of_k;  // K entries (entry 0 unused)
+};
+tvspec_status make_job(const tvspec_request &req, Job *out);
+
+// Device workspace of one image: one allocation carved into the arrays below.
+struct Slot {
+    int H = 0, W = 0, pitch = 0, K = 0, n_inner = 0, n_bands = 0, storage = 0;
+    bool trace = false, naive = false, async_alloc = false;
+    double dt = 0.0;
+    char *base = nullptr;
+    size_t bytes = 0;
+    size_t zero_off = 0, zero_bytes = 0;  // region cleared at the start of every decomposition
+    float *f = nullptr;
+    void *p1[2] = {nullptr, nullptr}, *p2[2] = {nullptr, nullptr};  // two copies of p
+    float *gl = nullptr;
+    double *ua = nullptr, *ub = nullptr, *acc = nullptr;
+    float *bands = nullptr, *residual = nullptr;
+    double *S = nullptr, *utrace = nullptr, *partials = nullptr;
+    unsigned *counter = nullptr, *status = nullptr;
+    signed char *band_of_k = nullptr;
+    int ep_blocks = 0;
+    size_t p_bytes = 0;  // bytes of one pitched p array (one component, one copy)
+};
+size_t slot_bytes_for(const Job &j, int storage, bool naive);
+tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStream_t st,
+                         bool async_alloc);
+void slot_free(Slot *s, cudaStream_t st);
+ImgDesc slot_desc(const Slot &s, int s0);
+
+// Device tables of one set of images: descriptors, tiles of one tile shape, epilogue blocks.
+// Images are kept in the given order; prefix arrays give the first tile / epilogue block of
+// each image so that a prefix of the images maps to a prefix of each table.
+struct LaunchSet {
+    int n = 0, shape = -1, depth = 0;
+    ImgDesc *d_descs = nullptr;
+    TileRef *d_tiles = nullptr;
+    int *d_ep_img = nullptr, *d_ep_base = nullptr;
+    size_t cap_descs = 0, cap_tiles = 0, cap_ep = 0;
+    std::vector<ImgDesc> h_descs;
+    std::vector<int> tile_prefix, ep_prefix;
+    void release();
+};
+// Builds and uploads (synchronously) the tables for descs with tile shape `shape` (-1: none).
+tvspec_status launchset_build(LaunchSet *ls, const std::vector<ImgDesc> &descs, int shape,
+                              int depth);
+// Tiles of one image for a shape: (ceil(W/ow), ceil(H/oh)).
+void tiles_for(int shape, int H, int W, int *ntx, int *nty);
+
+struct CacheEntry {
+    std::string key;
+    std::vector<Slot> slots;     // in run order (sorted by K, descending)
+    std::vector<int> order;      // order[i] = index of the caller's request in slot i
+    LaunchSet ls;
+    int maxK = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t graph_kernels = 0;
+    unsigned *h_status = nullptr;  // pinned, one word per image
+};
+
+struct Server;  // serving scheduler (serving.cu)
+
+}  // namespace tvspec
+
+struct tvspec_plan {
+    // second copy of the dual field for tvspec_chambolle_iterate on caller buffers
+    void *ping = nullptr;
+    size_t ping_bytes = 0;
+    int device = 0;
+    tvspec_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::mutex mu;  // serialises the plain and batched paths
+    std::list<std::unique_ptr<tvspec::CacheEntry>> cache;  // most recent first
+    std::map<std::string, std::pair<int, int>> tune;         // key -> (shape, depth)
+    std::map<std::string, std::unique_ptr<tvspec::LaunchSet>> iter_sets;
+    std::list<tvspec::Slot> scratch;                        // buffers of tvspec_rof_step etc.
+    std::atomic<uint64_t> kernel_launches{0}, graph_launches{0}, graphs_built{0},
+        decompositions{0};
+    std::atomic<int> last_tile{-1}, last_depth{0};
+    tvspec::Server *server = nullptr;  // created on first submit, freed by tvspec_server_stop
+    std::mutex server_mu;
+};
+
+namespace tvspec {
+
+// Chooses (shape, depth) for a set of slots (autotuned unless the config fixes them).
+tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, cudaStream_t st,
+                           int *shape, int *depth);
+
+// Enqueues the device work of one ROF step at global step gstep for the first n_active images
+// of the set (dual iterations + epilogue). Adds the kernels launched to *n_kernels.
+tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *> &slots,
+                           int n_active, int gstep, cudaStream_t st, uint64_t *n_kernels);
+
+size_t plan_budget(const tvspec_plan *plan);
+
+}  // namespace tvspec

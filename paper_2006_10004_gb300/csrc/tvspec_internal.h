@@ -1,0 +1,128 @@
+// Internal data structures shared by the kernels and the host runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace tvspec {
+
+// Most band edges a request may carry (n_edges <= kMaxEdges).
+constexpr int kMaxEdges = 65;
+// Pixels of one row chunk handled by one epilogue block.
+constexpr int kEpBlock = 256;
+// Device status bits written by kernels into ImgDesc::status.
+constexpr unsigned kStatusNonFinite = 1u;
+
+// One image of a launch set. Lives in device memory; kernels read it, the epilogue updates
+// the per-image counter and status word.
+struct ImgDesc {
+    const float *f;         // input image (compact H*W), device
+    // dual field, storage type of the plan, pitched (pitch elements), two copies: every
+    // launch of dual iterations reads one copy and writes the other (tiles read halo pixels
+    // that neighbouring tiles of the same launch update)
+    void *p1[2], *p2[2];
+    float *gl;              // g / lambda of the current ROF step, float32, pitched
+    double *ua, *ub;        // u ping-pong (compact H*W): u_k is ua for even k, ub for odd k
+    double *acc;            // running sum of the active band (compact H*W)
+    float *bands;           // (n_bands) H W output (compact), device
+    float *residual;        // H W output (compact), device
+    double *S;              // K-1 output, device
+    double *u_trace;        // optional (K+1) H W output, device, or nullptr
+    double *partials;       // one partial |phi| sum per epilogue block
+    unsigned *counter;      // epilogue blocks finished in the current step
+    unsigned *status;       // device status bits
+    const signed char *band_of_k;  // K entries: band of t_k (host-decided in float64), -1 none
+    int H, W, pitch;
+    int K, n_inner;
+    int s0;                 // global step at which this image's step 0 runs
+    int n_bands;
+    int ep_blocks;          // epilogue blocks of this image (H * ceil(W / kEpBlock))
+    double dt;              // lambda of every step
+    double inv_dt;          // 1 / dt (float64)
+};
+
+// Copy of the dual field read by launch blk (0-based) of local step k when every step runs
+// nb = ceil(n_inner / depth) launches and step 0 starts from copy 0: the copy flips once per
+// launch, so launch blk of step k reads copy (k nb + blk) mod 2 and the epilogue of step k
+// reads copy ((k+1) nb) mod 2.
+__host__ __device__ __forceinline__ int p_copy(int k, int nb, int blk) {
+    return (((k & 1) & (nb & 1)) + blk) & 1;
+}
+__host__ __device__ __forceinline__ int launches_per_step(int n_inner, int depth) {
+    return (n_inner + depth - 1) / depth;
+}
+
+// One tile of the tiled dual-iteration kernel: image index and tile coordinates.
+struct TileRef {
+    int img;
+    int tx, ty;
+};
+
+// Storage conversions for the dual field.
+template <typename P> struct PStore;
+template <> struct PStore<float> {
+    static __device__ __forceinline__ float load(float x) { return x; }
+    static __device__ __forceinline__ float store(float x) { return x; }
+};
+template <> struct PStore<__half> {
+    static __device__ __forceinline__ float load(__half x) { return __half2float(x); }
+    static __device__ __forceinline__ __half store(float x) { return __float2half_rn(x); }
+};
+template <> struct PStore<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(__nv_bfloat16 x) { return __bfloat162float(x); }
+    static __device__ __forceinline__ __nv_bfloat16 store(float x) { return __float2bfloat16_rn(x); }
+};
+
+// ---- launchers (defined in the .cu files) -------------------------------------------------
+
+// Tile shapes available to the tiled kernel.
+struct TileShape {
+    int V;      // columns per lane
+    int R;      // rows per thread
+    int RW;     // warps per block (stacked vertically)
+    int TB;     // most iterations per launch (the halo width)
+};
+int tiled_shape_count();
+TileShape tiled_shape(int index);
+// Output tile (columns, rows) of a shape: (32 V - 2 roundup(TB, V), RW R - 2 TB).
+void tiled_output_tile(const TileShape &s, int *ow, int *oh);
+
+// Launch one tiled pass of global step gstep: every CTA advances its tile by
+// min(depth, n_inner - blk depth) iterations (depth <= the shape's TB), reading copy
+// p_copy(k, nb, blk) of the dual field and writing the other. p_storage: 0 fp32, 1 fp16, 2 bf16.
+cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *tiles, int n_tiles,
+                         const ImgDesc *descs, int gstep, int blk, int depth, float tau,
+                         cudaStream_t st);
+
+// One iteration per launch over one image (reference GPU kernel): p_in -> p_out.
+cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,
+                         void *p1_out, void *p2_out, const float *gl, int H, int W, int pitch,
+                         float tau, cudaStream_t st);
+
+// Start of a decomposition for every image owning a block of the ep_img/ep_base list:
+// u_0 = f, gl = f / dt, trace[0] = f; non-finite f sets kStatusNonFinite. p, acc and the
+// padding columns must already be zero.
+cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_base,
+                        int n_blocks, cudaStream_t st);
+
+// Per-step epilogue over every epilogue block listed in ep_img/ep_base (one entry per block):
+// u_{k+1} = u_k - dt div p, gl = u_{k+1}/dt, phi_k, S(t_k), band accumulation, residual.
+// Each image's local step is gstep - s0; images outside [0, K) are skipped.
+// `depth` is the iterations per launch of the step's dual iterations (1 for the reference
+// kernel); it tells the epilogue which copy of p holds the step's result.
+cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_img,
+                            const int *ep_base, int n_blocks, int gstep, int depth,
+                            cudaStream_t st);
+
+// One ROF step's primal recovery for the standalone ROF entry: u = g - lambda div p (float32
+// inputs, float32 output, compact layout for u and g, pitched p).
+cudaError_t launch_rof_primal(const float *p1, const float *p2, int pitch, const float *g,
+                              float *u, int H, int W, double lambda, cudaStream_t st);
+
+// Pitched copies between compact float images and pitched workspace arrays.
+cudaError_t launch_gl_from_g(const float *g, float *gl, int H, int W, int pitch, double lambda,
+                             cudaStream_t st);
+
+}  // namespace tvspec

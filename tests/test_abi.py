@@ -1,0 +1,98 @@
+"""The C ABI library: it builds, loads, exports every declared entry point, and its host-only
+argument checks behave as documented. None of these tests needs a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2006_10004_gb300 as tv
+
+INF = float("inf")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(tvspec_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    lib = tv.load()
+    names = _declared_functions()
+    assert "tvspec_decompose" in names and "tvspec_submit" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # every binding signature refers to a declared function and vice versa
+    assert set(tv._SIGS) == set(names)
+
+
+def test_status_strings_and_version():
+    lib = tv.load()
+    for code, name in tv.STATUS.items():
+        assert lib.tvspec_status_str(code).decode() == name
+    assert lib.tvspec_status_str(99).decode() == "TVSPEC_UNKNOWN"
+    assert b"sm_103a" in lib.tvspec_version()
+
+
+def test_tile_table():
+    shapes = tv.tile_shapes()
+    assert len(shapes) >= 8
+    for s in shapes:
+        assert s["V"] in (2, 4) and s["R"] * s["V"] <= 32 and 1 <= s["TB"] <= 16
+        hx = (s["TB"] + s["V"] - 1) // s["V"] * s["V"]
+        assert 32 * s["V"] - 2 * hx > 0 and s["RW"] * s["R"] - 2 * s["TB"] > 0
+    assert tv.load().tvspec_tile_info(len(shapes), None, None, None, None) == tv.EINVAL
+
+
+def test_validate_accepts_good_requests():
+    assert tv.validate((64, 64), 0.5, 20, 200, (0, 2, 5, 10, INF)) == tv.OK
+    assert tv.validate((1, 1), 1.0, 2, 0, (0, INF)) == tv.OK
+    assert tv.validate((3, 700), 0.25, 60, 300, (0, 1, 2, 4, 8, 16, INF)) == tv.OK
+    assert tv.validate((5, 5), 0.5, 4, 10, (0.5, 1.0, 3.0)) == tv.OK
+
+
+@pytest.mark.parametrize("kw", [
+    dict(f_shape=(0, 5)), dict(f_shape=(5, 0)), dict(K=1), dict(K=0), dict(dt=0.0), dict(dt=-1.0),
+    dict(dt=float("nan")), dict(dt=INF), dict(n_inner=-1), dict(edges=(0.0,)),
+    dict(edges=(0.0, 0.0, 1.0)), dict(edges=(0.0, 2.0, 1.0)), dict(edges=(-1.0, 1.0)),
+    dict(edges=(0.0, INF, 5.0)), dict(edges=(0.0, float("nan"))), dict(edges=tuple(range(70))),
+    dict(mem_kind=7),
+])
+def test_validate_rejects_bad_arguments(kw):
+    args = dict(f_shape=(8, 8), dt=0.5, K=4, n_inner=10, edges=(0, 1, INF))
+    args.update(kw)
+    assert tv.validate(**args) == tv.EINVAL
+    assert len(tv.load().tvspec_last_error()) > 0
+
+
+def test_validate_rejects_non_finite_host_image():
+    f = np.zeros((4, 4), np.float32)
+    f[2, 3] = np.nan
+    assert tv.validate((4, 4), 0.5, 4, 10, (0, INF), f=f) == tv.EINVAL
+    f[2, 3] = np.inf
+    assert tv.validate((4, 4), 0.5, 4, 10, (0, INF), f=f) == tv.EINVAL
+
+
+def test_null_arguments_are_rejected_without_a_gpu():
+    lib = tv.load()
+    assert lib.tvspec_validate(None) == tv.EINVAL
+    assert lib.tvspec_plan_create(None, 0, None) == tv.EINVAL
+    assert lib.tvspec_decompose_ex(None, None, None) == tv.EINVAL
+    assert lib.tvspec_decompose_batch(None, 0, None, None) == tv.EINVAL
+    assert lib.tvspec_poll(None, 1) == tv.EINVAL
+    assert lib.tvspec_plan_destroy(None) == tv.OK
+
+
+def test_plan_create_without_gpu_reports_ecuda():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tv.TvSpecError) as ei:
+        tv.Plan(0)
+    assert ei.value.status == tv.ECUDA

@@ -1,0 +1,294 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (Python binding = marshalling only).
+
+Parity bars are in ``tolerances.py``. Bit-identity tests check what the design promises:
+the result of the float32 dual iterations does not depend on the tile shape, the iterations
+per launch, graph replay, the memory mode, or the batch an image runs in.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from tolerances import assert_parity, parity_metrics
+
+pytestmark = pytest.mark.gpu
+INF = float("inf")
+
+
+@pytest.fixture(scope="module")
+def tv():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2006_10004_gb300 as tvm
+
+    tvm.load()
+    return tvm
+
+
+@pytest.fixture(scope="module")
+def plan(tv):
+    p = tv.Plan(0)
+    yield p
+    p.close()
+
+
+def _img(H, W, seed, n=6, r=(2.0, 12.0)):
+    return syn.make_image(H, W, n, r, (0.1, 1.0), 0.02, seed)
+
+
+def _same(a, b):
+    for k in ("bands", "residual", "S"):
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+    if "u" in a and "u" in b:
+        assert np.array_equal(np.asarray(a["u"]), np.asarray(b["u"])), "u"
+
+
+# ---------------------------------------------------------------------------------------------
+def test_config0_full_parity(plan):
+    job = syn.config0().jobs[0]
+    g = plan.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True)
+    ref = oracle.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True)
+    m = assert_parity(g, ref, job.f, "config0")
+    print("config0", m)
+
+
+@pytest.mark.parametrize("H,W", [(37, 53), (130, 70), (1, 1), (1, 17), (19, 1), (2, 3), (65, 129),
+                                 (200, 333)])
+def test_ragged_sizes_parity(plan, H, W):
+    f = _img(H, W, seed=H * 1000 + W)
+    g = plan.decompose(f, 0.5, 6, 25, syn.DYADIC_EDGES, trace=True)
+    ref = oracle.decompose(f, 0.5, 6, 25, syn.DYADIC_EDGES, trace=True)
+    assert_parity(g, ref, f, f"{H}x{W}")
+
+
+def test_constant_image_exact(plan):
+    f = np.full((40, 70), 0.3, np.float32)
+    g = plan.decompose(f, 0.5, 5, 40, syn.DYADIC_EDGES, trace=True)
+    assert np.all(g["bands"] == 0) and np.all(g["S"] == 0)
+    assert np.array_equal(g["residual"], f)
+    assert np.all(g["u"] == np.float64(np.float32(0.3)))
+
+
+def test_zero_inner_iterations(plan):
+    f = _img(20, 30, 3)
+    g = plan.decompose(f, 0.5, 4, 0, syn.DYADIC_EDGES)
+    assert np.all(g["bands"] == 0) and np.all(g["S"] == 0)
+    assert np.array_equal(g["residual"], f)
+
+
+def test_band_edges_not_covering_time_range(plan):
+    # a band set that starts after t_1 and ends before t_{K-1}: only the covered phi_k count
+    f = _img(33, 41, 4)
+    edges = (0.75, 1.5, 2.25)
+    g = plan.decompose(f, 0.25, 14, 30, edges, trace=True)
+    ref = oracle.decompose(f, 0.25, 14, 30, edges, trace=True)
+    m = parity_metrics(g, ref, f)
+    assert m["band_inf"] <= 1e-3 and m["u_inf"] <= 1e-4, m
+
+
+# ---------------------------------------------------------------------------------------------
+# bit-identity of the implementation choices
+# ---------------------------------------------------------------------------------------------
+def test_every_tile_shape_and_depth_bit_identical(tv):
+    f = _img(100, 150, 7)
+    args = (f, 0.5, 4, 23, syn.DYADIC_EDGES)
+    with tv.Plan(0, kernel=tv.KERNEL_NAIVE) as p:
+        base = p.decompose(*args, trace=True)
+    for i, s in enumerate(tv.tile_shapes()):
+        for depth in sorted({1, 3, s["TB"]}):
+            with tv.Plan(0, kernel=tv.KERNEL_TILED, tile=i, temporal_block=depth) as p:
+                out = p.decompose(*args, trace=True)
+                assert p.stats()["last_tile"] == i
+            _same(out, base)
+
+
+def test_many_waves_of_tiles_bit_identical_and_parity(tv):
+    # an image with many more tiles than the GPU holds at once: later tiles read halos that
+    # earlier tiles of the same launch have already finished (the ping-pong copies of p must
+    # make that irrelevant), and the run must be reproducible
+    f = syn.make_image(1000, 1100, 120, (2.0, 60.0), (0.05, 1.0), 0.02, seed=77)
+    args = (f, 0.5, 3, 40, syn.DYADIC_EDGES)
+    with tv.Plan(0, kernel=tv.KERNEL_NAIVE) as p:
+        base = p.decompose(*args, trace=True)
+    for tile in (0, 5, 10, 11):
+        with tv.Plan(0, kernel=tv.KERNEL_TILED, tile=tile) as p:
+            a = p.decompose(*args, trace=True)
+            b = p.decompose(*args, trace=True)
+        _same(a, base)
+        _same(b, base)
+    ref = oracle.decompose(*args, trace=True)
+    assert_parity(base, ref, f, "1000x1100")
+
+
+def test_graph_and_plain_launches_bit_identical(tv):
+    f = _img(90, 77, 8)
+    args = (f, 0.5, 5, 31, syn.DYADIC_EDGES)
+    with tv.Plan(0, use_graphs=1) as a, tv.Plan(0, use_graphs=0) as b:
+        ra = a.decompose(*args, trace=True)
+        ra2 = a.decompose(*args, trace=True)  # graph replay
+        rb = b.decompose(*args, trace=True)
+        assert a.stats()["graph_launches"] == 2 and b.stats()["graph_launches"] == 0
+    _same(ra, rb)
+    _same(ra, ra2)
+
+
+def test_device_and_host_memory_bit_identical(plan):
+    import torch
+
+    f = _img(64, 96, 9)
+    h = plan.decompose(f, 0.5, 6, 30, syn.DYADIC_EDGES, trace=True)
+    ft = torch.from_numpy(f).cuda()
+    d = plan.decompose(ft, 0.5, 6, 30, syn.DYADIC_EDGES, trace=True)
+    torch.cuda.synchronize()
+    _same(h, {k: v.cpu().numpy() for k, v in d.items()})
+
+
+def test_batch_matches_alone_bit_identical_and_oracle(plan):
+    rng = np.random.default_rng(11)
+    jobs = []
+    for j in range(7):
+        H, W = int(rng.integers(20, 140)), int(rng.integers(20, 140))
+        K = int(rng.integers(3, 9))
+        dt = float(rng.choice([0.25, 0.5, 1.0]))
+        jobs.append((_img(H, W, 100 + j), dt, K, 30, syn.DYADIC_EDGES))
+    outs = plan.decompose_batch(jobs, trace=True)
+    for job, out in zip(jobs, outs):
+        alone = plan.decompose(*job, trace=True)
+        _same(out, alone)
+        ref = oracle.decompose(*job, trace=True)
+        assert_parity(out, ref, job[0])
+
+
+# ---------------------------------------------------------------------------------------------
+# invariances (Sec. 2.1), exact on the GPU path too
+# ---------------------------------------------------------------------------------------------
+def test_one_homogeneity_exact(plan):
+    f = _img(70, 50, 12)
+    e = (0.0, 1.0, 2.0, 4.0, INF)
+    a = plan.decompose(f, 0.5, 7, 40, e, trace=True)
+    b = plan.decompose(2 * f, 1.0, 7, 40, tuple(2 * x for x in e), trace=True)
+    assert np.array_equal(b["u"], 2 * a["u"])
+    assert np.array_equal(b["bands"], 2 * a["bands"])
+    assert np.array_equal(b["residual"], 2 * a["residual"])
+    assert np.array_equal(b["S"], a["S"])
+
+
+def test_transpose_exact(plan):
+    f = _img(45, 77, 13)
+    a = plan.decompose(f, 0.5, 6, 35, syn.DYADIC_EDGES)
+    b = plan.decompose(np.ascontiguousarray(f.T), 0.5, 6, 35, syn.DYADIC_EDGES)
+    assert np.array_equal(b["bands"], np.transpose(a["bands"], (0, 2, 1)))
+    assert np.array_equal(b["residual"], a["residual"].T)
+    np.testing.assert_allclose(b["S"], a["S"], rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------------------------
+# the ROF step alone (Eq. ROF by Chambolle's iterations)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n_iter", [1, 7, 100, 1000])
+def test_rof_step_matches_oracle(plan, n_iter):
+    g = _img(48, 40, 14)
+    u, p1, p2 = plan.rof_step(g, 0.5, n_iter)
+    ru, rp1, rp2 = oracle.chambolle(g, 0.5, n_iter)
+    assert np.abs(u - ru).max() <= 1e-5 * max(1.0, np.abs(g).max())
+    assert np.abs(p1 - rp1).max() <= 1e-5 and np.abs(p2 - rp2).max() <= 1e-5
+
+
+def test_rof_step_warm_start_input(plan):
+    g = _img(30, 33, 15)
+    _, p1, p2 = oracle.chambolle(g, 0.7, 40)
+    u, q1, q2 = plan.rof_step(g, 0.7, 60, p1, p2)
+    ru, _, _ = oracle.chambolle(g, 0.7, 60, p1=p1, p2=p2)
+    assert np.abs(u - ru).max() <= 1e-5
+
+
+# ---------------------------------------------------------------------------------------------
+# full sizes
+# ---------------------------------------------------------------------------------------------
+def test_config1_full_size_parity(plan):
+    job = syn.config1().jobs[0]
+    g = plan.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True)
+    ref = oracle.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True)
+    m = assert_parity(g, ref, job.f, "config1")
+    print("config1", m)
+
+
+def test_config3_full_size_first_steps_parity(plan):
+    # full 2048^2 spatial size and iteration count, the first 3 ROF steps (the oracle's share)
+    job = syn.config3().jobs[0]
+    g = plan.decompose(job.f, job.dt, 3, job.n_inner, job.edges, trace=True)
+    ref = oracle.decompose(job.f, job.dt, 3, job.n_inner, job.edges, trace=True)
+    assert_parity(g, ref, job.f, "config3 K=3")
+
+
+def test_config3_full_run_properties(plan):
+    # the whole 2048^2, K=50, 500-iteration run: reconstruction and exact one-homogeneity
+    job = syn.config3().jobs[0]
+    a = plan.decompose(job.f, job.dt, job.K, job.n_inner, job.edges)
+    rec = a["bands"].astype(np.float64).sum(0) + a["residual"]
+    assert np.abs(rec - job.f).max() <= 1e-5 * np.abs(job.f).max()
+    assert np.all(np.isfinite(a["S"])) and np.all(a["S"] >= 0)
+    b = plan.decompose(2 * job.f, 2 * job.dt, job.K, job.n_inner, tuple(2 * e for e in job.edges))
+    assert np.array_equal(b["bands"], 2 * a["bands"]) and np.array_equal(b["S"], a["S"])
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_16bit_dual_storage_reports_error(tv, storage):
+    # fp16 / bf16 storage of p between launches: errors are reported, no bar is promised;
+    # the reconstruction identity holds regardless (it telescopes in float64)
+    job = syn.config1(H=256, W=256, K=20).jobs[0]
+    with tv.Plan(0, p_storage=storage) as p:
+        g = p.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True)
+    ref = oracle.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True)
+    m = parity_metrics(g, ref, job.f)
+    print("p_storage", storage, m)
+    assert m["recon_inf"] <= 1e-5
+    assert m["u_inf"] < 1.0
+
+
+# ---------------------------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------------------------
+def test_serving_results_match_alone(tv):
+    rng = np.random.default_rng(21)
+    jobs = []
+    for j in range(8):
+        s = int(rng.choice([48, 64, 96, 130]))
+        jobs.append((_img(s, s + 7, 200 + j), 0.5, int(rng.integers(3, 8)), 30, syn.DYADIC_EDGES))
+    with tv.Plan(0) as p:
+        tickets = [p.submit(*j, trace=True) for j in jobs]
+        for (t, out), job in zip(tickets, jobs):
+            assert p.wait(t, 120000) == tv.OK
+        st = p.serving_stats()
+        assert st["count"] == len(jobs) and st["p99_ms"] >= st["p50_ms"] > 0
+        for (t, out), job in zip(tickets, jobs):
+            alone = p.decompose(*job, trace=True)
+            _same(out, alone)
+
+
+def test_serving_budget_and_cancel(tv):
+    f = _img(64, 64, 30)
+    with tv.Plan(0, mem_budget_bytes=1 << 16) as p:
+        t, _ = p.submit(f, 0.5, 4, 10, syn.DYADIC_EDGES)
+        assert p.wait(t, 60000) == tv.ENOMEM
+    with tv.Plan(0, max_batch=1) as p:
+        t1, _ = p.submit(_img(256, 256, 31), 0.5, 40, 300, syn.DYADIC_EDGES)
+        t2, _ = p.submit(f, 0.5, 4, 10, syn.DYADIC_EDGES)
+        assert p.cancel(t2) == tv.OK
+        assert p.wait(t2, 60000) == tv.ECANCELLED
+        assert p.wait(t1, 120000) == tv.OK
+        assert p.poll(12345) == tv.EINVAL
+
+
+def test_invalid_arguments_leave_plan_usable(plan, tv):
+    f = _img(16, 16, 40)
+    with pytest.raises(tv.TvSpecError) as ei:
+        plan.decompose(f, 0.5, 1, 10, syn.DYADIC_EDGES)
+    assert ei.value.status == tv.EINVAL
+    bad = f.copy()
+    bad[3, 3] = np.nan
+    with pytest.raises(tv.TvSpecError):
+        plan.decompose(bad, 0.5, 4, 10, syn.DYADIC_EDGES)
+    out = plan.decompose(f, 0.5, 4, 10, syn.DYADIC_EDGES)
+    assert np.all(np.isfinite(out["bands"]))
