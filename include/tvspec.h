@@ -183,6 +183,35 @@ tvspec_status tvspec_rof_step(tvspec_plan *plan, const float *g, int H, int W, d
 tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float *p1, float *p2,
                                        int H, int W, int pitch, int n_iter, void *stream);
 
+/* The decomposition without any device allocation. No counterpart in the paper: this entry
+ * exists for callers that cannot call cudaMalloc/cudaFree where they run (a thread working
+ * while another captures a CUDA graph in global mode, real-time loops that cannot take the
+ * implicit synchronisation of an allocation, frameworks that own all device memory).
+ *
+ * f (H*W), bands ((n_edges-1)*H*W), residual (H*W) and S (K-1) are DEVICE pointers on the
+ * current CUDA device, caller-owned. Every other buffer comes from one file-scope device array
+ * of 48 MiB inside this library, which every GPU that loads the library holds until the
+ * process exits. Arithmetic and defaults are those of a default plan (float32 dual
+ * iterations, float64 epilogue, tau = 1/8, warm start), and the results equal
+ * tvspec_decompose with such a plan.
+ *
+ * Limits: 1 <= H, W <= 2048, 2 <= K <= 4096, and the workspace (about 44 bytes per pixel plus
+ * small tables) must fit the 48 MiB array -- about 1.1 megapixels, so 1024x1024 fits and
+ * 2048x2048 does not; larger requests return TVSPEC_EINVAL with the needed size in
+ * tvspec_last_error().
+ *
+ * The call enqueues its work on `stream` (a cudaStream_t; NULL = the legacy default stream)
+ * and returns; the outputs are valid once the stream reaches that point. It allocates nothing:
+ * the first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress) -- make that first call before any stream capture. Every call uses
+ * the same array and finds the previous call's contents in it (the call clears what must
+ * start at zero), so calls that overlap on the GPU race: issue them on one stream, or
+ * synchronise between them. A non-finite value in f is not detected (it propagates).
+ * Errors: EINVAL, ENOTSUP, ECUDA. */
+tvspec_status tvspec_decompose_noalloc(const float *f, int H, int W, double dt, int K,
+                                       int n_inner, const double *band_edges, int n_edges,
+                                       float *bands, float *residual, double *S, void *stream);
+
 /* Number of tile shapes this build provides for TVSPEC_KERNEL_TILED, and the geometry of
  * shape `index`: columns per lane, rows per thread, warps per block, maximum iterations per
  * launch. Returns EINVAL for an index out of range. */

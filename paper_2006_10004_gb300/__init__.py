@@ -87,6 +87,10 @@ _SIGS = {
     "tvspec_chambolle_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_void_p]),
+    "tvspec_decompose_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
     "tvspec_tile_count": (ctypes.c_int, []),
     "tvspec_tile_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -337,6 +341,31 @@ class Plan:
         s = Stats()
         _check(self._lib.tvspec_plan_stats(self._h, ctypes.byref(s)), "tvspec_plan_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def decompose_noalloc(f, dt: float, K: int, n_inner: int, edges, stream=None) -> Result:
+    """The decomposition through tvspec_decompose_noalloc, which allocates no device memory.
+
+    For callers that may not call cudaMalloc where they run (see include/tvspec.h). ``f`` is a
+    2-D float32 CUDA tensor; the outputs are allocated here by torch, outside the entry point,
+    as such a caller would pre-allocate them. Images up to about 1.1 megapixels.
+    """
+    import torch
+
+    L = load()
+    f = f.contiguous()
+    if f.dtype != torch.float32 or f.dim() != 2 or not f.is_cuda:
+        raise TypeError("f must be a 2-D float32 CUDA tensor")
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+    H, W = f.shape
+    out = Result(bands=torch.empty((len(e) - 1, H, W), dtype=torch.float32, device=f.device),
+                 residual=torch.empty((H, W), dtype=torch.float32, device=f.device),
+                 S=torch.empty((max(K - 1, 1),), dtype=torch.float64, device=f.device))
+    _check(L.tvspec_decompose_noalloc(f.data_ptr(), H, W, float(dt), int(K), int(n_inner), e.ctypes.data, len(e),
+                                      out["bands"].data_ptr(), out["residual"].data_ptr(), out["S"].data_ptr(),
+                                      _stream_ptr(stream)), "tvspec_decompose_noalloc")
+    out["S"] = out["S"][: max(K - 1, 0)]
+    return out
 
 
 def validate(f_shape, dt, K, n_inner, edges, f=None, mem_kind=MEM_HOST) -> int:
