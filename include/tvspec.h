@@ -75,6 +75,7 @@ typedef struct {
     int fast_math;          /* 1 (default): hardware approximate sqrt/reciprocal; 0: IEEE-rounded */
     size_t mem_budget_bytes;/* device memory the serving scheduler may hold; 0 = 60 GiB */
     int max_batch;          /* serving: most requests resident at once; 0 = 256 */
+    int pdl;                /* 1: programmatic dependent launch between the kernels of a step; default 0 */
 } tvspec_config;
 
 /* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in

@@ -13,6 +13,12 @@
 
 namespace tvspec {
 
+// Programmatic dependent launch: wait until the preceding grid has completed and its memory
+// is visible (a no-op when the launch has no programmatic dependency), and allow the next
+// grid in the stream to be scheduled while this one runs.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Hardware approximate square root / reciprocal (PTX sqrt.approx, rcp.approx).
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
@@ -43,6 +49,46 @@ __device__ __forceinline__ void tv_update(float &p1, float &p2, float G1, float 
     float s = FAST ? rcp_approx(den) : __frcp_rn(den);
     p1 = __fmul_rn(__fmaf_rn(tau, G1, p1), s);
     p2 = __fmul_rn(__fmaf_rn(tau, G2, p2), s);
+}
+
+// ---- the same arithmetic on two pixels at once (Blackwell packed f32x2 instructions) ----
+// Each lane of a packed operation rounds exactly like the scalar intrinsic above: a - b is
+// computed as fma(b, -1, a), which is the correctly rounded difference, and no packed product
+// feeds a packed sum (see sq_norm2). So tv_w2 / tv_update2 give the same bits as
+// tv_w / tv_update applied to .x and .y separately.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+
+__device__ __forceinline__ float2 tv_w2(float2 p1, float2 p1_up, float2 p2, float2 p2_left,
+                                        float2 gl) {
+    return sub2(__fadd2_rn(sub2(p1, p1_up), sub2(p2, p2_left)), gl);
+}
+
+// |G|^2 = G1*G1 + G2*G2 on a pixel pair: packed products, scalar sums. A product feeding a
+// sum may be fused into one multiply-add by the compiler when both are packed; with the sums
+// done by the scalar rounded addition each lane equals the scalar
+// __fadd_rn(__fmul_rn(G1, G1), __fmul_rn(G2, G2)), which the tests check bit for bit.
+__device__ __forceinline__ float2 sq_norm2(float2 G1, float2 G2) {
+    const float2 a = __fmul2_rn(G1, G1);
+    const float2 b = __fmul2_rn(G2, G2);
+    return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+}
+
+template <bool FAST>
+__device__ __forceinline__ void tv_update2(float2 &p1, float2 &p2, float2 G1, float2 G2,
+                                           float tau) {
+    const float2 n2 = sq_norm2(G1, G2);
+    float2 nrm;
+    nrm.x = FAST ? sqrt_approx(n2.x) : __fsqrt_rn(n2.x);
+    nrm.y = FAST ? sqrt_approx(n2.y) : __fsqrt_rn(n2.y);
+    const float2 t2 = make_float2(tau, tau);
+    const float2 den = __ffma2_rn(t2, nrm, make_float2(1.0f, 1.0f));
+    float2 s;
+    s.x = FAST ? rcp_approx(den.x) : __frcp_rn(den.x);
+    s.y = FAST ? rcp_approx(den.y) : __frcp_rn(den.y);
+    p1 = __fmul2_rn(__ffma2_rn(t2, G1, p1), s);
+    p2 = __fmul2_rn(__ffma2_rn(t2, G2, p2), s);
 }
 
 }  // namespace tvspec

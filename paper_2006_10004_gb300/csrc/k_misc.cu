@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(kEpBlock)
                const int *__restrict__ ep_base, int gstep, int depth) {
     __shared__ double s_red[kEpBlock / 32];
     __shared__ int s_last;
+    pdl_wait();  // the step's last dual-iteration launch must be complete
+    pdl_trigger();
     const int b = blockIdx.x;
     const int img = ep_img[b];
     ImgDesc *d = descs + img;
@@ -203,16 +205,24 @@ __global__ void __launch_bounds__(kEpBlock)
 
 cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_img,
                             const int *ep_base, int n_blocks, int gstep, int depth,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool pdl) {
     if (n_blocks <= 0) return cudaSuccess;
     ImgDesc *dd = const_cast<ImgDesc *>(descs);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_blocks);
+    cfg.blockDim = dim3(kEpBlock);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
     switch (p_storage) {
-        case 0: k_epilogue<float><<<n_blocks, kEpBlock, 0, st>>>(dd, ep_img, ep_base, gstep, depth); break;
-        case 1: k_epilogue<__half><<<n_blocks, kEpBlock, 0, st>>>(dd, ep_img, ep_base, gstep, depth); break;
-        case 2: k_epilogue<__nv_bfloat16><<<n_blocks, kEpBlock, 0, st>>>(dd, ep_img, ep_base, gstep, depth); break;
+        case 0: return cudaLaunchKernelEx(&cfg, k_epilogue<float>, dd, ep_img, ep_base, gstep, depth);
+        case 1: return cudaLaunchKernelEx(&cfg, k_epilogue<__half>, dd, ep_img, ep_base, gstep, depth);
+        case 2: return cudaLaunchKernelEx(&cfg, k_epilogue<__nv_bfloat16>, dd, ep_img, ep_base, gstep, depth);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------

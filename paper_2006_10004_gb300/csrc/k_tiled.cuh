@@ -35,75 +35,87 @@ struct alignas(sizeof(float) * V) FPack {
     float v[V];
 };
 
+// The iterations of one launch on the registers of one thread. Pixels are processed in
+// horizontal pairs (columns 2q, 2q+1 of the lane) with packed f32x2 arithmetic.
 template <int V, int R, int RW, bool FAST, bool EDGE>
-__device__ __forceinline__ void tiled_iterate(float (&p1)[R][V], float (&p2)[R][V],
-                                              const float (&gl)[R][V], int n_iter, float tau,
-                                              unsigned m1bits, unsigned m2bits,
+__device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
+                                              const float2 (&gl)[R][V / 2], int n_iter,
+                                              float tau, unsigned m1bits, unsigned m2bits,
                                               float (*s_p1b)[32 * V], float (*s_wt)[32 * V],
                                               int lane, int wy) {
     constexpr unsigned FULL = 0xffffffffu;
-    float w[R][V];
+    constexpr int VP = V / 2;
+    float2 w[R][VP];
     for (int it = 0; it < n_iter; ++it) {
         // ---- w = div p - g/lambda on every owned pixel
-        float up[V];
+        float2 up[VP];
         if (RW > 1 && wy > 0) {
             FPack<V> q = *reinterpret_cast<const FPack<V> *>(&s_p1b[wy - 1][lane * V]);
 #pragma unroll
-            for (int v = 0; v < V; ++v) up[v] = q.v[v];
+            for (int j = 0; j < VP; ++j) up[j] = make_float2(q.v[2 * j], q.v[2 * j + 1]);
         } else {
 #pragma unroll
-            for (int v = 0; v < V; ++v) up[v] = 0.0f;  // tile top row: halo
+            for (int j = 0; j < VP; ++j) up[j] = make_float2(0.0f, 0.0f);  // tile top row: halo
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float left0 = __shfl_up_sync(FULL, p2[r][V - 1], 1);
+            const float left0 = __shfl_up_sync(FULL, p2[r][VP - 1].y, 1);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const float p1u = (r == 0) ? up[v] : p1[r - 1][v];
-                const float p2l = (v == 0) ? left0 : p2[r][v - 1];
-                w[r][v] = tv_w(p1[r][v], p1u, p2[r][v], p2l, gl[r][v]);
+            for (int j = 0; j < VP; ++j) {
+                const float2 p1u = (r == 0) ? up[j] : p1[r - 1][j];
+                const float2 p2l = make_float2(j == 0 ? left0 : p2[r][j - 1].y, p2[r][j].x);
+                w[r][j] = tv_w2(p1[r][j], p1u, p2[r][j], p2l, gl[r][j]);
             }
         }
-        float dn[V];
+        float2 dn[VP];
         if (RW > 1) {
             FPack<V> q;
 #pragma unroll
-            for (int v = 0; v < V; ++v) q.v[v] = w[0][v];
+            for (int j = 0; j < VP; ++j) {
+                q.v[2 * j] = w[0][j].x;
+                q.v[2 * j + 1] = w[0][j].y;
+            }
             *reinterpret_cast<FPack<V> *>(&s_wt[wy][lane * V]) = q;
             __syncthreads();
             if (wy < RW - 1) {
                 FPack<V> b = *reinterpret_cast<const FPack<V> *>(&s_wt[wy + 1][lane * V]);
 #pragma unroll
-                for (int v = 0; v < V; ++v) dn[v] = b.v[v];
+                for (int j = 0; j < VP; ++j) dn[j] = make_float2(b.v[2 * j], b.v[2 * j + 1]);
             } else {
 #pragma unroll
-                for (int v = 0; v < V; ++v) dn[v] = w[R - 1][v];  // tile bottom row: halo
+                for (int j = 0; j < VP; ++j) dn[j] = w[R - 1][j];  // tile bottom row: halo
             }
         } else {
 #pragma unroll
-            for (int v = 0; v < V; ++v) dn[v] = w[R - 1][v];
+            for (int j = 0; j < VP; ++j) dn[j] = w[R - 1][j];
         }
         // ---- p <- (p + tau grad w) / (1 + tau |grad w|)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float right_last = __shfl_down_sync(FULL, w[r][0], 1);
+            const float right_last = __shfl_down_sync(FULL, w[r][0].x, 1);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const float wd = (r < R - 1) ? w[r + 1][v] : dn[v];
-                const float wr = (v < V - 1) ? w[r][v + 1] : right_last;
-                float G1 = __fsub_rn(wd, w[r][v]);
-                float G2 = __fsub_rn(wr, w[r][v]);
+            for (int j = 0; j < VP; ++j) {
+                const float2 wd = (r < R - 1) ? w[r + 1][j] : dn[j];
+                const float2 wr = make_float2(w[r][j].y, j < VP - 1 ? w[r][j + 1].x : right_last);
+                float2 G1 = sub2(wd, w[r][j]);
+                float2 G2 = sub2(wr, w[r][j]);
                 if (EDGE) {
-                    G1 = ((m1bits >> (r * V + v)) & 1u) ? G1 : 0.0f;
-                    G2 = ((m2bits >> (r * V + v)) & 1u) ? G2 : 0.0f;
+                    const int b0 = r * V + 2 * j;
+                    G1.x = ((m1bits >> b0) & 1u) ? G1.x : 0.0f;
+                    G1.y = ((m1bits >> (b0 + 1)) & 1u) ? G1.y : 0.0f;
+                    G2.x = ((m2bits >> b0) & 1u) ? G2.x : 0.0f;
+                    G2.y = ((m2bits >> (b0 + 1)) & 1u) ? G2.y : 0.0f;
                 }
-                tv_update<FAST>(p1[r][v], p2[r][v], G1, G2, tau);
+                tv_update2<FAST>(p1[r][j], p2[r][j], G1, G2, tau);
             }
         }
         if (RW > 1) {
             FPack<V> q;
 #pragma unroll
-            for (int v = 0; v < V; ++v) q.v[v] = p1[R - 1][v];
+            for (int j = 0; j < VP; ++j) {
+                q.v[2 * j] = p1[R - 1][j].x;
+                q.v[2 * j + 1] = p1[R - 1][j].y;
+            }
             *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
             __syncthreads();
         }
@@ -115,6 +127,8 @@ __global__ void __launch_bounds__(32 * RW)
     k_tiled(const TileRef *__restrict__ tiles, const ImgDesc *__restrict__ descs, int gstep,
             int blk, int depth, float tau) {
     static_assert(R * V <= 32, "mask bits");
+    static_assert(V % 2 == 0, "pixels are processed in pairs");
+    constexpr int VP = V / 2;
     constexpr int TW = 32 * V;
     constexpr int TH = RW * R;
     constexpr int HX = (TB + V - 1) / V * V;
@@ -124,6 +138,9 @@ __global__ void __launch_bounds__(32 * RW)
     __shared__ __align__(16) float s_p1b[RW][TW];
     __shared__ __align__(16) float s_wt[RW][TW];
 
+    // nothing below may read what the preceding launch wrote before this point
+    pdl_wait();
+    pdl_trigger();
     const TileRef t = tiles[blockIdx.x];
     const ImgDesc *d = descs + t.img;
     const int H = d->H, W = d->W, pitch = d->pitch;
@@ -147,7 +164,7 @@ __global__ void __launch_bounds__(32 * RW)
     const int ry = ys + wy * R;
     const bool col_ok = (cx >= 0) && (cx < pitch);
 
-    float p1[R][V], p2[R][V], gl[R][V];
+    float2 p1[R][VP], p2[R][VP], gl[R][VP];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int y = ry + r;
@@ -157,20 +174,23 @@ __global__ void __launch_bounds__(32 * RW)
             PPack<P, V> b = *reinterpret_cast<const PPack<P, V> *>(gp2 + off);
             FPack<V> c = *reinterpret_cast<const FPack<V> *>(ggl + off);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                p1[r][v] = PStore<P>::load(a.v[v]);
-                p2[r][v] = PStore<P>::load(b.v[v]);
-                gl[r][v] = c.v[v];
+            for (int j = 0; j < VP; ++j) {
+                p1[r][j] = make_float2(PStore<P>::load(a.v[2 * j]), PStore<P>::load(a.v[2 * j + 1]));
+                p2[r][j] = make_float2(PStore<P>::load(b.v[2 * j]), PStore<P>::load(b.v[2 * j + 1]));
+                gl[r][j] = make_float2(c.v[2 * j], c.v[2 * j + 1]);
             }
         } else {
 #pragma unroll
-            for (int v = 0; v < V; ++v) p1[r][v] = p2[r][v] = gl[r][v] = 0.0f;
+            for (int j = 0; j < VP; ++j) p1[r][j] = p2[r][j] = gl[r][j] = make_float2(0.0f, 0.0f);
         }
     }
     if (RW > 1) {
         FPack<V> q;
 #pragma unroll
-        for (int v = 0; v < V; ++v) q.v[v] = p1[R - 1][v];
+        for (int j = 0; j < VP; ++j) {
+            q.v[2 * j] = p1[R - 1][j].x;
+            q.v[2 * j + 1] = p1[R - 1][j].y;
+        }
         *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
         __syncthreads();
     }
@@ -206,9 +226,11 @@ __global__ void __launch_bounds__(32 * RW)
                 const size_t off = (size_t)y * pitch + cx;
                 PPack<P, V> a, b;
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    a.v[v] = PStore<P>::store(p1[r][v]);
-                    b.v[v] = PStore<P>::store(p2[r][v]);
+                for (int j = 0; j < VP; ++j) {
+                    a.v[2 * j] = PStore<P>::store(p1[r][j].x);
+                    a.v[2 * j + 1] = PStore<P>::store(p1[r][j].y);
+                    b.v[2 * j] = PStore<P>::store(p2[r][j].x);
+                    b.v[2 * j + 1] = PStore<P>::store(p2[r][j].y);
                 }
                 *reinterpret_cast<PPack<P, V> *>(op1 + off) = a;
                 *reinterpret_cast<PPack<P, V> *>(op2 + off) = b;

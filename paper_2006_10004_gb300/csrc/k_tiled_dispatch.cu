@@ -23,7 +23,7 @@ void tiled_output_tile(const TileShape &s, int *ow, int *oh) {
 
 cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *tiles, int n_tiles,
                          const ImgDesc *descs, int gstep, int blk, int depth, float tau,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool pdl) {
     if (shape < 0 || shape >= tiled_shape_count()) return cudaErrorInvalidValue;
     if (n_tiles <= 0) return cudaSuccess;
     TiledKernel k = nullptr;
@@ -35,8 +35,17 @@ cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *til
     }
     if (!k) return cudaErrorInvalidValue;
     const int threads = 32 * kShapes[shape].RW;
-    k<<<n_tiles, threads, 0, st>>>(tiles, descs, gstep, blk, depth, tau);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_tiles);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, tiles, descs, gstep, blk, depth, tau);
 }
 
 }  // namespace tvspec

@@ -427,7 +427,7 @@ static tvspec_status enqueue_iterations(tvspec_plan *plan, LaunchSet &ls,
     const int nt = ls.tile_prefix[n_active];
     for (int b = 0; b < nblk; ++b) {
         cudaError_t e = launch_tiled(ls.shape, c.p_storage, c.fast_math != 0, ls.d_tiles, nt,
-                                     ls.d_descs, gstep, b, ls.depth, c.tau, st);
+                                     ls.d_descs, gstep, b, ls.depth, c.tau, st, c.pdl != 0);
         if (e != cudaSuccess) return fail_cuda(e, "tiled kernel launch");
         ++*nk;
     }
@@ -450,7 +450,8 @@ tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *>
     tvspec_status s = enqueue_iterations(plan, ls, slots, n_active, gstep, st, nk);
     if (s != TVSPEC_OK) return s;
     cudaError_t e = launch_epilogue(c.p_storage, ls.d_descs, ls.d_ep_img, ls.d_ep_base,
-                                    ls.ep_prefix[n_active], gstep, ls.shape < 0 ? 1 : ls.depth, st);
+                                    ls.ep_prefix[n_active], gstep, ls.shape < 0 ? 1 : ls.depth, st,
+                                    c.pdl != 0);
     if (e != cudaSuccess) return fail_cuda(e, "epilogue launch");
     if (ls.ep_prefix[n_active] > 0) ++*nk;
     return TVSPEC_OK;
@@ -760,6 +761,7 @@ void tvspec_config_init(tvspec_config *cfg) {
     cfg->fast_math = 1;
     cfg->mem_budget_bytes = 0;
     cfg->max_batch = 0;
+    cfg->pdl = 0;
 }
 
 tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_plan **out) {

@@ -92,9 +92,11 @@ void tiled_output_tile(const TileShape &s, int *ow, int *oh);
 // Launch one tiled pass of global step gstep: every CTA advances its tile by
 // min(depth, n_inner - blk depth) iterations (depth <= the shape's TB), reading copy
 // p_copy(k, nb, blk) of the dual field and writing the other. p_storage: 0 fp32, 1 fp16, 2 bf16.
+// With pdl, the launch may start while the preceding kernel in the stream drains
+// (programmatic dependent launch); the kernels wait for it before touching any data.
 cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *tiles, int n_tiles,
                          const ImgDesc *descs, int gstep, int blk, int depth, float tau,
-                         cudaStream_t st);
+                         cudaStream_t st, bool pdl = false);
 
 // One iteration per launch over one image (reference GPU kernel): p_in -> p_out.
 cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,
@@ -114,7 +116,7 @@ cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_b
 // kernel); it tells the epilogue which copy of p holds the step's result.
 cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_img,
                             const int *ep_base, int n_blocks, int gstep, int depth,
-                            cudaStream_t st);
+                            cudaStream_t st, bool pdl = false);
 
 // One ROF step's primal recovery for the standalone ROF entry: u = g - lambda div p (float32
 // inputs, float32 output, compact layout for u and g, pitched p).

@@ -133,6 +133,13 @@ def test_graph_and_plain_launches_bit_identical(tv):
     _same(ra, ra2)
 
 
+def test_programmatic_dependent_launch_bit_identical(tv):
+    f = _img(160, 140, 10)
+    args = (f, 0.5, 5, 37, syn.DYADIC_EDGES)
+    with tv.Plan(0, pdl=1) as a, tv.Plan(0, pdl=0) as b:
+        _same(a.decompose(*args, trace=True), b.decompose(*args, trace=True))
+
+
 def test_device_and_host_memory_bit_identical(plan):
     import torch
 
