@@ -178,6 +178,10 @@ def run_gb300(args):
 
     if args.kernel_only:
         return run_kernel_only(args, tv, torch, local)
+    if args.workload == "config2":
+        return run_batched(args, tv, torch, local, ws)
+    if args.workload == "config4":
+        return run_serving(args, tv, torch, local, ws)
     wl = _workload(args.workload)
     plan = tv.Plan(local)
     dev = torch.device("cuda", local)
@@ -321,6 +325,139 @@ def run_gb300(args):
     return 0
 
 
+def run_batched(args, tv, torch, local, ws):
+    """Config 2: 64 images of uneven sizes and schedules. Images/s of the batched path
+    (one set of launches per step over all images, graph-replayed) against the plain path
+    (the same images decomposed one at a time, each graph-replayed), same device buffers."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    wl = syn.config2()
+    jobs = [(torch.from_numpy(j.f).to(dev), j.dt, j.K, j.n_inner, j.edges) for j in wl.jobs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    plan = tv.Plan(local)
+
+    def timed(fn, steps):
+        evs = []
+        with ClockSampler(local) as clk:
+            for i in range(steps):
+                flush.fill_(i & 0xff)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in evs) / 1000.0, clk.summary()
+
+    batch = lambda: plan.decompose_batch(jobs, stream=stream)
+    for _ in range(args.warmup):
+        batch()
+    torch.cuda.synchronize()
+    s0 = plan.stats()
+    t_batch, clk = timed(batch, args.steps)
+    s1 = plan.stats()
+    plain_plan = tv.Plan(local)
+
+    def plain():
+        for j in jobs:
+            plain_plan.decompose(*j, stream=stream)
+
+    plain()
+    torch.cuda.synchronize()
+    t_plain, _ = timed(plain, max(1, args.steps // 2))
+    n_img = len(jobs)
+    px_it = wl.px_iters
+    value = px_it * args.steps / t_batch / 1e6
+    result = {"metric": "Chambolle Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": ws,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_batch / args.steps,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+              "data": "synthetic",
+              "config": {"workload": wl.name, "images": n_img, "l2": "flushed before every timed step",
+                         "tile": s1["last_tile"], "temporal_block": s1["last_temporal_block"]},
+              "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]), "clocks": clk,
+              "batched": {"images_per_s": n_img * args.steps / t_batch,
+                          "ms_per_batch": 1000 * t_batch / args.steps},
+              "plain_one_at_a_time": {"images_per_s": n_img * max(1, args.steps // 2) / t_plain,
+                                      "ms_per_batch": 1000 * t_plain / max(1, args.steps // 2)}}
+    result["batched_over_plain"] = result["batched"]["images_per_s"] / result["plain_one_at_a_time"]["images_per_s"]
+    print(json.dumps(result))
+    plan.close()
+    plain_plan.close()
+    return 0
+
+
+def run_serving(args, tv, torch, local, ws):
+    """Config 4: Poisson arrivals of single-image requests (sizes 256^2..2048^2 with weights
+    .4/.3/.2/.1, K ~ U{20..50}, dt .5, 300 iterations, 6 bands) into the serving loop
+    (continuous batching, 60 GiB budget). For each rate: images/s and p50/p99 latency
+    (submit to finish, host clock), and the same requests through the plain path one at a
+    time for images/s. A pool of 8 images per size is reused (timing does not depend on the
+    picture)."""
+    import random
+
+    rates = [float(x) for x in args.rates.split(",")]
+    n_req = args.requests
+    pool = {}
+    for s in (256, 512, 1024, 2048):
+        pool[s] = [syn.make_image(s, s, max(1, int(40 * s * s / 512 ** 2)), (2.0, 60.0), (0.05, 1.0), 0.02,
+                                  4000 + 10 * s + k) for k in range(8)]
+    out = {"metric": "served images/s and p50/p99 latency", "workload": "config4_serving", "n_gpus": ws,
+           "requests_per_rate": n_req, "data": "synthetic", "load_points": []}
+    for rate in rates:
+        rng = np.random.default_rng(4000 + int(rate))
+        arrivals, jobs = [], []
+        t = 0.0
+        for j in range(n_req):
+            t += float(rng.exponential(1.0 / rate))
+            s = int(rng.choice([256, 512, 1024, 2048], p=[0.4, 0.3, 0.2, 0.1]))
+            K = int(rng.integers(20, 51))
+            arrivals.append(t)
+            jobs.append((pool[s][j % 8], 0.5, K, 300, syn.DYADIC_EDGES))
+        px_it = sum(j[0].size * j[2] * j[3] for j in jobs)
+        with tv.Plan(local) as plan:
+            # warm the scheduler thread and its tile choice
+            tw, _ = plan.submit(*jobs[0])
+            plan.wait(tw)
+            plan.serving_stats(reset=True)
+            tickets = []
+            t0 = time.perf_counter()
+            with ClockSampler(local) as clk:
+                for a, job in zip(arrivals, jobs):
+                    dt_wait = t0 + a - time.perf_counter()
+                    if dt_wait > 0:
+                        time.sleep(dt_wait)
+                    tickets.append(plan.submit(*job)[0])
+                for tk in tickets:
+                    st = plan.wait(tk)
+                    if st != 0:
+                        raise SystemExit(f"served request failed: {st}")
+            wall = time.perf_counter() - t0
+            lat = plan.serving_stats()
+        with tv.Plan(local) as plain:
+            for job in jobs[:8]:
+                plain.decompose(*job)
+            t1 = time.perf_counter()
+            for job in jobs:
+                plain.decompose(*job)
+            t_plain = time.perf_counter() - t1
+            # the same requests as one offline batch: the ceiling of batching them
+            plain.decompose_batch(jobs[:4])
+            t2 = time.perf_counter()
+            plain.decompose_batch(jobs)
+            t_batch = time.perf_counter() - t2
+        out["load_points"].append({"rate_req_per_s": rate, "served_images_per_s": n_req / wall,
+                                   "served_Mpx_iter_per_s": px_it / wall / 1e6,
+                                   "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "count": lat["count"],
+                                   "plain_images_per_s": n_req / t_plain,
+                                   "offline_batch_images_per_s": n_req / t_batch,
+                                   "plain_Mpx_iter_per_s": px_it / t_plain / 1e6,
+                                   "offered_duration_s": arrivals[-1], "wall_s": wall, "clocks": clk.summary()})
+        print(json.dumps(out["load_points"][-1]), flush=True)
+    print(json.dumps(out))
+    return 0
+
+
 def run_kernel_only(args, tv, torch, local):
     """The dual-iteration kernel alone on an N x N image (config-1 generator, shapes scaled
     with the area): a small, self-contained case for profiler captures."""
@@ -362,7 +499,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="config1", choices=["config1", "m1024", "config2", "config3"])
+    ap.add_argument("--workload", default="config1", choices=["config1", "m1024", "config2", "config3", "config4"])
+    ap.add_argument("--rates", default="20,50,100,200", help="config4: Poisson arrival rates (req/s)")
+    ap.add_argument("--requests", type=int, default=200, help="config4: requests per rate")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-k", type=int, default=50, help="ROF steps of the oracle's CPU sample")

@@ -68,8 +68,8 @@ cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void
 
 __global__ void __launch_bounds__(kEpBlock)
     k_init(ImgDesc *__restrict__ descs, const int *__restrict__ ep_img,
-           const int *__restrict__ ep_base) {
-    const int b = blockIdx.x;
+           const int *__restrict__ ep_base, int block_offset) {
+    const int b = blockIdx.x + block_offset;
     const int img = ep_img[b];
     ImgDesc *d = descs + img;
     const int lb = b - ep_base[img];
@@ -88,9 +88,10 @@ __global__ void __launch_bounds__(kEpBlock)
 }
 
 cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_base,
-                        int n_blocks, cudaStream_t st) {
+                        int n_blocks, cudaStream_t st, int block_offset) {
     if (n_blocks <= 0) return cudaSuccess;
-    k_init<<<n_blocks, kEpBlock, 0, st>>>(const_cast<ImgDesc *>(descs), ep_img, ep_base);
+    k_init<<<n_blocks, kEpBlock, 0, st>>>(const_cast<ImgDesc *>(descs), ep_img, ep_base,
+                                          block_offset);
     return cudaGetLastError();
 }
 

@@ -252,7 +252,13 @@ __global__ void __launch_bounds__(32 * RW)
     X(8, 2, 8, 4, 4)          \
     X(9, 4, 4, 16, 12)        \
     X(10, 2, 8, 16, 12)       \
-    X(11, 2, 4, 8, 2)
+    X(11, 2, 4, 8, 2)         \
+    X(12, 2, 4, 16, 8)        \
+    X(13, 2, 4, 32, 8)        \
+    X(14, 2, 2, 32, 8)        \
+    X(15, 4, 2, 32, 8)        \
+    X(16, 2, 4, 16, 4)        \
+    X(17, 2, 4, 32, 12)
 
 using TiledKernel = void (*)(const TileRef *, const ImgDesc *, int, int, int, float);
 

@@ -688,6 +688,19 @@ static tvspec_status scratch_slot(tvspec_plan *plan, int H, int W, Slot **out) {
     return TVSPEC_OK;
 }
 
+tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *depth) {
+    std::lock_guard<std::mutex> lock(plan->mu);
+    TV_CK(cudaSetDevice(plan->device));
+    Slot *sl = nullptr;
+    tvspec_status s = scratch_slot(plan, H, W, &sl);
+    if (s != TVSPEC_OK) return s;
+    std::vector<Slot *> sp{sl};
+    s = choose_tiles(plan, sp, plan->stream, shape, depth);
+    if (s != TVSPEC_OK) return s;
+    TV_CK(cudaStreamSynchronize(plan->stream));
+    return TVSPEC_OK;
+}
+
 // Runs d.n_inner dual iterations as local step 0 of the image described by d (two copies of
 // p, copy 0 holding the start); *final_copy receives the copy holding the result.
 static tvspec_status run_iterations(tvspec_plan *plan, ImgDesc d, cudaStream_t st,

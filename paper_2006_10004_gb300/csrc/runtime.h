@@ -129,4 +129,7 @@ tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *>
 
 size_t plan_budget(const tvspec_plan *plan);
 
+// Tile choice for an H x W image, tuned on plan-owned scratch buffers (takes the plan lock).
+tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *depth);
+
 }  // namespace tvspec

@@ -1,16 +1,23 @@
 // Serving: continuous batching of single-image decompositions at ROF-step boundaries.
 //
 // A scheduler thread owns the device work of served requests. Each tick it
-//   1. retires cancelled requests,
+//   1. takes cancelled requests out of the resident set,
 //   2. admits waiting requests (FIFO) while their workspace fits the memory budget and the
-//      number of resident requests stays below max_batch, uploads their images and starts
-//      them (u_0 = f) at the current global step,
+//      number of resident requests stays below max_batch, allocates their workspace
+//      (stream-ordered), uploads their images and starts them (u_0 = f) at the current
+//      global step,
 //   3. runs one ROF step (all dual iterations + the epilogue) for every resident request in
 //      one set of launches over the tiles of all of them,
-//   4. copies out the requests that just finished their K-th step and frees their workspace.
+//   4. hands the requests whose K-th step was just enqueued to a retire thread.
+// The retire thread waits for a request's last step on its own stream, copies the outputs
+// to the caller's buffers, frees the workspace and signals completion, while the scheduler
+// keeps the compute stream busy with the next ticks. Launch tables are double-buffered:
+// a table is rebuilt only after the event recorded behind its last use has completed.
+//
 // Requests therefore join and leave while others are mid-flight; each request's arithmetic
 // is the same as when it runs alone (tiling-invariant dual iterations, per-image reductions
-// in a fixed order), so its results are bit-identical.
+// in a fixed order), so its results are bit-identical. The tile shape is the configured one,
+// or tuned once on a 2048 x 2048 image under the plan lock.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -24,32 +31,42 @@ using Clock = std::chrono::steady_clock;
 struct ServeReq {
     uint64_t ticket = 0;
     Job job;
-    int state = 0;  // 0 queued, 1 running, 2 finished (result below)
+    int state = 0;  // 0 queued, 1 resident or retiring, 2 finished (result below)
     bool cancel = false;
     tvspec_status result = TVSPEC_ENOTREADY;
+    tvspec_status pending = TVSPEC_OK;  // result to report once retired
     Clock::time_point t_submit, t_done;
     Slot slot;
     int s0 = 0;
     size_t bytes = 0;
+    cudaEvent_t done_ev = nullptr;
 };
 
 struct Server {
     tvspec_plan *plan = nullptr;
-    std::thread th;
+    std::thread th, retire_th;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_retire;
     std::deque<std::shared_ptr<ServeReq>> waiting;
     std::vector<std::shared_ptr<ServeReq>> active;  // scheduler thread only
+    std::deque<std::shared_ptr<ServeReq>> retire_q;
     std::map<uint64_t, std::shared_ptr<ServeReq>> all;
     uint64_t next_ticket = 1;
-    bool stop = false;
+    bool stop = false, retire_stop = false;
     size_t used = 0;
     std::vector<double> lat_ms;
-    cudaStream_t st = nullptr;
-    LaunchSet ls, init_ls;
+    cudaStream_t st = nullptr;   // compute
+    cudaStream_t cst = nullptr;  // copies out
+    LaunchSet ls[2];
+    cudaEvent_t ls_ev[2] = {nullptr, nullptr};
+    bool ls_used[2] = {false, false};
+    int cur = 0;
     int gstep = 0;
     int shape = -2, depth = 1;
     void loop();
+    void retire_loop();
+    void hand_to_retire(const std::shared_ptr<ServeReq> &r, tvspec_status pending);
+    void fail_all_active(tvspec_status s);
 };
 
 static void finish(Server *S, const std::shared_ptr<ServeReq> &r, tvspec_status result) {
@@ -63,30 +80,72 @@ static void finish(Server *S, const std::shared_ptr<ServeReq> &r, tvspec_status 
     S->cv_done.notify_all();
 }
 
-// Copies the outputs of a request that finished on the device to its host buffers.
-static tvspec_status copy_out(Server *S, ServeReq &r) {
+// The request's work is enqueued on the compute stream; record its completion and queue it
+// for the retire thread.
+void Server::hand_to_retire(const std::shared_ptr<ServeReq> &r, tvspec_status pending) {
+    r->pending = pending;
+    if (cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(r->done_ev, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (r->done_ev) cudaEventDestroy(r->done_ev);
+        r->done_ev = nullptr;
+        cudaStreamSynchronize(st);  // fall back to waiting here
+        if (r->pending == TVSPEC_OK) r->pending = TVSPEC_ECUDA;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        retire_q.push_back(r);
+    }
+    cv_retire.notify_one();
+}
+
+void Server::fail_all_active(tvspec_status s) {
+    for (auto &r : active) hand_to_retire(r, s);
+    active.clear();
+}
+
+// Copies the outputs of a finished request to its host buffers on the copy stream.
+static tvspec_status copy_out(cudaStream_t cst, ServeReq &r) {
     const tvspec_request &q = r.job.r;
     const size_t N = (size_t)q.H * q.W;
-    TV_CK(cudaMemcpyAsync(q.bands, r.slot.bands, (size_t)r.slot.n_bands * N * 4, cudaMemcpyDeviceToHost, S->st));
-    TV_CK(cudaMemcpyAsync(q.residual, r.slot.residual, N * 4, cudaMemcpyDeviceToHost, S->st));
-    TV_CK(cudaMemcpyAsync(q.S, r.slot.S, (size_t)(q.K - 1) * 8, cudaMemcpyDeviceToHost, S->st));
+    TV_CK(cudaMemcpyAsync(q.bands, r.slot.bands, (size_t)r.slot.n_bands * N * 4, cudaMemcpyDeviceToHost, cst));
+    TV_CK(cudaMemcpyAsync(q.residual, r.slot.residual, N * 4, cudaMemcpyDeviceToHost, cst));
+    TV_CK(cudaMemcpyAsync(q.S, r.slot.S, (size_t)(q.K - 1) * 8, cudaMemcpyDeviceToHost, cst));
     if (q.u_trace)
-        TV_CK(cudaMemcpyAsync(q.u_trace, r.slot.utrace, (size_t)(q.K + 1) * N * 8, cudaMemcpyDeviceToHost, S->st));
+        TV_CK(cudaMemcpyAsync(q.u_trace, r.slot.utrace, (size_t)(q.K + 1) * N * 8, cudaMemcpyDeviceToHost, cst));
     unsigned status = 0;
-    TV_CK(cudaMemcpyAsync(&status, r.slot.status, sizeof(unsigned), cudaMemcpyDeviceToHost, S->st));
-    TV_CK(cudaStreamSynchronize(S->st));
+    TV_CK(cudaMemcpyAsync(&status, r.slot.status, sizeof(unsigned), cudaMemcpyDeviceToHost, cst));
+    TV_CK(cudaStreamSynchronize(cst));
     if (status & kStatusNonFinite) return fail(TVSPEC_ECUDA, "non-finite value in the flow");
     return TVSPEC_OK;
 }
 
-static void fail_all_active(Server *S, tvspec_status s) {
-    for (auto &r : S->active) {
-        slot_free(&r->slot, S->st);
-        S->used -= r->bytes;
-        finish(S, r, s);
+void Server::retire_loop() {
+    cudaSetDevice(plan->device);
+    for (;;) {
+        std::shared_ptr<ServeReq> r;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_retire.wait(lk, [&] { return retire_stop || !retire_q.empty(); });
+            if (retire_q.empty()) break;  // retire_stop and nothing left
+            r = retire_q.front();
+            retire_q.pop_front();
+        }
+        if (r->done_ev) cudaStreamWaitEvent(cst, r->done_ev, 0);
+        tvspec_status res = r->pending;
+        if (res == TVSPEC_OK) res = copy_out(cst, *r);
+        slot_free(&r->slot, cst);  // stream-ordered after the copies and the last step
+        if (r->done_ev) cudaEventDestroy(r->done_ev);
+        r->done_ev = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            used -= r->bytes;
+        }
+        if (res == TVSPEC_OK) plan->decompositions++;
+        finish(this, r, res);
+        cv_work.notify_all();  // memory came free: waiting requests may fit now
     }
-    S->active.clear();
-    cudaStreamSynchronize(S->st);
+    cudaStreamSynchronize(cst);
 }
 
 void Server::loop() {
@@ -94,14 +153,15 @@ void Server::loop() {
     const tvspec_config &c = plan->cfg;
     const int max_batch = c.max_batch > 0 ? c.max_batch : 256;
     const size_t budget = plan_budget(plan);
+    for (int i = 0; i < 2; ++i) cudaEventCreateWithFlags(&ls_ev[i], cudaEventDisableTiming);
     bool changed = true;
     for (;;) {
         std::vector<std::shared_ptr<ServeReq>> admitted;
+        std::vector<std::shared_ptr<ServeReq>> cancelled;
         {
             std::unique_lock<std::mutex> lk(mu);
             cv_work.wait(lk, [&] { return stop || !waiting.empty() || !active.empty(); });
             if (stop) break;
-            // cancelled requests still waiting
             for (auto it = waiting.begin(); it != waiting.end();) {
                 if ((*it)->cancel) {
                     (*it)->result = TVSPEC_ECANCELLED;
@@ -116,7 +176,7 @@ void Server::loop() {
             while (!waiting.empty() && (int)(active.size() + admitted.size()) < max_batch) {
                 auto &r = waiting.front();
                 if (used + r->bytes > budget) {
-                    if (active.empty() && admitted.empty()) {
+                    if (active.empty() && admitted.empty() && used == 0) {
                         // can never fit: reject rather than wait forever
                         r->result = fail(TVSPEC_ENOMEM, "request exceeds the serving memory budget");
                         r->state = 2;
@@ -132,27 +192,15 @@ void Server::loop() {
                 admitted.push_back(r);
                 waiting.pop_front();
             }
+            for (auto &r : active)
+                if (r->cancel) cancelled.push_back(r);
         }
-        // running requests cancelled since the last tick
-        for (size_t i = 0; i < active.size();) {
-            bool cancel;
-            {
-                std::lock_guard<std::mutex> lk(mu);
-                cancel = active[i]->cancel;
-            }
-            if (cancel) {
-                auto r = active[i];
-                cudaStreamSynchronize(st);
-                slot_free(&r->slot, st);
-                used -= r->bytes;
-                active.erase(active.begin() + i);
-                finish(this, r, TVSPEC_ECANCELLED);
-                changed = true;
-            } else {
-                ++i;
-            }
+        for (auto &r : cancelled) {
+            active.erase(std::find(active.begin(), active.end(), r));
+            hand_to_retire(r, TVSPEC_ECANCELLED);
+            changed = true;
         }
-        // admission: workspace, image upload, u_0 = f
+        // admission: workspace, image upload
         std::vector<std::shared_ptr<ServeReq>> started;
         for (auto &r : admitted) {
             tvspec_status s = slot_alloc(&r->slot, r->job, c.p_storage, false, st, true);
@@ -167,83 +215,81 @@ void Server::loop() {
                 }
             }
             if (s != TVSPEC_OK) {
-                used -= r->bytes;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    used -= r->bytes;
+                }
                 finish(this, r, s);
                 continue;
             }
             r->s0 = gstep;
             started.push_back(r);
         }
-        if (!started.empty()) {
-            std::vector<ImgDesc> nd;
-            for (auto &r : started) nd.push_back(slot_desc(r->slot, r->s0));
-            if (cudaStreamSynchronize(st) != cudaSuccess ||
-                launchset_build(&init_ls, nd, -1, 1) != TVSPEC_OK ||
-                launch_init(init_ls.d_descs, init_ls.d_ep_img, init_ls.d_ep_base,
-                            init_ls.ep_prefix[init_ls.n], st) != cudaSuccess) {
-                for (auto &r : started) {
-                    slot_free(&r->slot, st);
-                    used -= r->bytes;
-                    finish(this, r, fail(TVSPEC_ECUDA, "request start"));
-                }
-                started.clear();
-            } else {
-                plan->kernel_launches++;
-            }
-            for (auto &r : started) active.push_back(r);
-            changed = changed || !started.empty();
+        for (auto &r : started) active.push_back(r);
+        if (!started.empty()) changed = true;
+        if (active.empty()) {
+            // nothing resident: the queue head waits for memory a retiring request holds;
+            // sleep until the retire thread (or a submit / stop) signals
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            continue;
         }
-        if (active.empty()) continue;
-        std::vector<Slot *> sp;
-        for (auto &r : active) sp.push_back(&r->slot);
-        if (changed) {
-            if (cudaStreamSynchronize(st) != cudaSuccess) {
-                fail_all_active(this, fail(TVSPEC_ECUDA, "stream error"));
-                continue;
+        if (shape == -2) {
+            // one tile choice for all mixes: tuned on a 2048 x 2048 image, the size class
+            // that carries most of the served pixels (every shape gives the same bits)
+            if (c.tile >= 0) {
+                std::vector<Slot *> none;
+                if (choose_tiles(plan, none, st, &shape, &depth) != TVSPEC_OK) shape = -2;
+            } else if (tune_for_size(plan, 2048, 2048, &shape, &depth) != TVSPEC_OK) {
+                shape = -2;
             }
             if (shape == -2) {
-                // tile choice once, on the first request's shape; every shape gives the same bits
-                std::vector<Slot *> one{sp[0]};
-                if (choose_tiles(plan, one, st, &shape, &depth) != TVSPEC_OK) {
-                    fail_all_active(this, TVSPEC_ECUDA);
-                    shape = -2;
-                    continue;
-                }
-                // the tuner used the first request's buffers: restart it cleanly
-                Slot &s0 = active[0]->slot;
-                cudaMemsetAsync(s0.base + s0.zero_off, 0, s0.zero_bytes, st);
-                std::vector<ImgDesc> d0{slot_desc(s0, active[0]->s0)};
-                launchset_build(&init_ls, d0, -1, 1);
-                launch_init(init_ls.d_descs, init_ls.d_ep_img, init_ls.d_ep_base,
-                            init_ls.ep_prefix[1], st);
+                fail_all_active(TVSPEC_ECUDA);
+                continue;
             }
+        }
+        if (changed) {
+            const int nb = cur ^ 1;
+            if (ls_used[nb]) cudaEventSynchronize(ls_ev[nb]);  // its last tick is done
             std::vector<ImgDesc> descs;
             for (auto &r : active) descs.push_back(slot_desc(r->slot, r->s0));
-            if (cudaStreamSynchronize(st) != cudaSuccess ||
-                launchset_build(&ls, descs, shape, depth) != TVSPEC_OK) {
-                fail_all_active(this, TVSPEC_ECUDA);
+            if (launchset_build(&ls[nb], descs, shape, depth) != TVSPEC_OK) {
+                fail_all_active(TVSPEC_ECUDA);
                 continue;
+            }
+            cur = nb;
+            if (!started.empty()) {
+                // the newly started images are the last ones of the set
+                const int first = (int)(active.size() - started.size());
+                const int n = (int)active.size();
+                const int b0 = ls[cur].ep_prefix[first];
+                if (launch_init(ls[cur].d_descs, ls[cur].d_ep_img, ls[cur].d_ep_base,
+                                ls[cur].ep_prefix[n] - b0, st, b0) != cudaSuccess) {
+                    fail_all_active(fail(TVSPEC_ECUDA, "request start"));
+                    continue;
+                }
+                plan->kernel_launches++;
             }
             changed = false;
         }
+        std::vector<Slot *> sp;
+        for (auto &r : active) sp.push_back(&r->slot);
         uint64_t nk = 0;
-        tvspec_status s = enqueue_step(plan, ls, sp, (int)active.size(), gstep, st, &nk);
+        tvspec_status s = enqueue_step(plan, ls[cur], sp, (int)active.size(), gstep, st, &nk);
         plan->kernel_launches += nk;
+        cudaEventRecord(ls_ev[cur], st);
+        ls_used[cur] = true;
         if (s != TVSPEC_OK) {
-            fail_all_active(this, s);
+            fail_all_active(s);
             changed = true;
             continue;
         }
-        // retire the requests whose last step just ran
+        // requests whose last step was just enqueued leave the resident set
         for (size_t i = 0; i < active.size();) {
             auto r = active[i];
             if (gstep - r->s0 == r->job.r.K - 1) {
-                tvspec_status cs = copy_out(this, *r);
-                slot_free(&r->slot, st);
-                used -= r->bytes;
+                hand_to_retire(r, TVSPEC_OK);
                 active.erase(active.begin() + i);
-                plan->decompositions++;
-                finish(this, r, cs);
                 changed = true;
             } else {
                 ++i;
@@ -251,13 +297,8 @@ void Server::loop() {
         }
         ++gstep;
     }
-    // shutdown: cancel everything still resident or queued
-    cudaStreamSynchronize(st);
-    for (auto &r : active) {
-        slot_free(&r->slot, st);
-        finish(this, r, TVSPEC_ECANCELLED);
-    }
-    active.clear();
+    // shutdown: everything resident is cancelled, everything queued too
+    fail_all_active(TVSPEC_ECANCELLED);
     {
         std::lock_guard<std::mutex> lk(mu);
         for (auto &r : waiting) {
@@ -265,11 +306,16 @@ void Server::loop() {
             r->state = 2;
         }
         waiting.clear();
+        retire_stop = true;
         cv_done.notify_all();
     }
+    cv_retire.notify_all();
+    if (retire_th.joinable()) retire_th.join();
     cudaStreamSynchronize(st);
-    ls.release();
-    init_ls.release();
+    for (int i = 0; i < 2; ++i) {
+        ls[i].release();
+        if (ls_ev[i]) cudaEventDestroy(ls_ev[i]);
+    }
 }
 
 }  // namespace tvspec
@@ -294,6 +340,7 @@ void tvspec_server_stop(tvspec_plan *plan) {
     if (S->th.joinable()) S->th.join();
     cudaSetDevice(plan->device);
     cudaStreamDestroy(S->st);
+    cudaStreamDestroy(S->cst);
     delete S;
 }
 
@@ -305,10 +352,20 @@ static tvspec_status get_server(tvspec_plan *plan, Server **out) {
         if (!S) return fail(TVSPEC_ENOMEM, "server allocation");
         S->plan = plan;
         cudaError_t e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cst, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
+            if (S->st) cudaStreamDestroy(S->st);
             delete S;
-            return fail_cuda(e, "serving stream");
+            return fail_cuda(e, "serving streams");
         }
+        // keep memory freed by retired requests in the stream-ordered pool for the next ones
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, plan->device) == cudaSuccess) {
+            uint64_t keep = plan_budget(plan);
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+        S->retire_th = std::thread([S] { S->retire_loop(); });
         S->th = std::thread([S] { S->loop(); });
         plan->server = S;
     }
@@ -346,13 +403,14 @@ static std::shared_ptr<ServeReq> find(Server *S, uint64_t t) {
     return it == S->all.end() ? nullptr : it->second;
 }
 
+static Server *server_of(tvspec_plan *plan) {
+    std::lock_guard<std::mutex> lk(plan->server_mu);
+    return plan->server;
+}
+
 tvspec_status tvspec_poll(tvspec_plan *plan, uint64_t ticket) {
     if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
-    Server *S = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(plan->server_mu);
-        S = plan->server;
-    }
+    Server *S = server_of(plan);
     if (!S) return fail(TVSPEC_EINVAL, "unknown ticket");
     std::lock_guard<std::mutex> lk(S->mu);
     auto r = find(S, ticket);
@@ -362,11 +420,7 @@ tvspec_status tvspec_poll(tvspec_plan *plan, uint64_t ticket) {
 
 tvspec_status tvspec_wait(tvspec_plan *plan, uint64_t ticket, int timeout_ms) {
     if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
-    Server *S = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(plan->server_mu);
-        S = plan->server;
-    }
+    Server *S = server_of(plan);
     if (!S) return fail(TVSPEC_EINVAL, "unknown ticket");
     std::unique_lock<std::mutex> lk(S->mu);
     auto r = find(S, ticket);
@@ -382,11 +436,7 @@ tvspec_status tvspec_wait(tvspec_plan *plan, uint64_t ticket, int timeout_ms) {
 
 tvspec_status tvspec_cancel(tvspec_plan *plan, uint64_t ticket) {
     if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
-    Server *S = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(plan->server_mu);
-        S = plan->server;
-    }
+    Server *S = server_of(plan);
     if (!S) return fail(TVSPEC_EINVAL, "unknown ticket");
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -401,11 +451,7 @@ tvspec_status tvspec_cancel(tvspec_plan *plan, uint64_t ticket) {
 tvspec_status tvspec_serving_stats(tvspec_plan *plan, int reset, uint64_t *count, double *p50_ms,
                                    double *p99_ms) {
     if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
-    Server *S = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(plan->server_mu);
-        S = plan->server;
-    }
+    Server *S = server_of(plan);
     std::vector<double> v;
     if (S) {
         std::lock_guard<std::mutex> lk(S->mu);

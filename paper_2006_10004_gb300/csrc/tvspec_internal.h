@@ -103,11 +103,12 @@ cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void
                          void *p1_out, void *p2_out, const float *gl, int H, int W, int pitch,
                          float tau, cudaStream_t st);
 
-// Start of a decomposition for every image owning a block of the ep_img/ep_base list:
+// Start of a decomposition for every image owning one of the epilogue blocks
+// [block_offset, block_offset + n_blocks) of the ep_img/ep_base list:
 // u_0 = f, gl = f / dt, trace[0] = f; non-finite f sets kStatusNonFinite. p, acc and the
 // padding columns must already be zero.
 cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_base,
-                        int n_blocks, cudaStream_t st);
+                        int n_blocks, cudaStream_t st, int block_offset = 0);
 
 // Per-step epilogue over every epilogue block listed in ep_img/ep_base (one entry per block):
 // u_{k+1} = u_k - dt div p, gl = u_{k+1}/dt, phi_k, S(t_k), band accumulation, residual.

@@ -27,13 +27,21 @@ DYADIC_EDGES = (0.0, 1.0, 2.0, 4.0, 8.0, 16.0, INF)
 
 def make_image(H: int, W: int, n_shapes: int, r_range, c_range=(0.1, 1.0), sigma: float = 0.01,
                seed: int = 0) -> np.ndarray:
-    """Piecewise-constant disks/rectangles + Gaussian noise, float32 (see module docstring)."""
+    """Piecewise-constant disks/rectangles + Gaussian noise, float32 (see module docstring).
+
+    Each shape's pixel test is evaluated only inside its bounding box (plus one pixel); the
+    test itself, and so the image, is the same as evaluating it everywhere.
+    """
     rng = np.random.default_rng(seed)
     img = np.zeros((H, W), dtype=np.float64)
-    ii = (np.arange(H, dtype=np.float64) + 0.5)[:, None]
-    jj = (np.arange(W, dtype=np.float64) + 0.5)[None, :]
     r_lo, r_hi = r_range
     c_lo, c_hi = c_range
+
+    def box(c, h, n):
+        lo = max(0, int(np.floor(c - h - 0.5)) - 1)
+        hi = min(n, int(np.ceil(c + h - 0.5)) + 2)
+        return lo, hi
+
     for _ in range(n_shapes):
         is_disk = rng.random() < 0.5
         cy = rng.uniform(0.0, H)
@@ -41,12 +49,21 @@ def make_image(H: int, W: int, n_shapes: int, r_range, c_range=(0.1, 1.0), sigma
         c = rng.uniform(c_lo, c_hi)
         if is_disk:
             r = rng.uniform(r_lo, r_hi)
+            i0, i1 = box(cy, r, H)
+            j0, j1 = box(cx, r, W)
+            ii = (np.arange(i0, i1, dtype=np.float64) + 0.5)[:, None]
+            jj = (np.arange(j0, j1, dtype=np.float64) + 0.5)[None, :]
             mask = (ii - cy) ** 2 + (jj - cx) ** 2 <= r * r
         else:
             hy = rng.uniform(r_lo, r_hi)
             hx = rng.uniform(r_lo, r_hi)
+            i0, i1 = box(cy, hy, H)
+            j0, j1 = box(cx, hx, W)
+            ii = (np.arange(i0, i1, dtype=np.float64) + 0.5)[:, None]
+            jj = (np.arange(j0, j1, dtype=np.float64) + 0.5)[None, :]
             mask = (np.abs(ii - cy) <= hy) & (np.abs(jj - cx) <= hx)
-        img[mask] = c
+        if i1 > i0 and j1 > j0:
+            img[i0:i1, j0:j1][mask] = c
     if sigma > 0:
         img = img + rng.normal(0.0, sigma, size=(H, W))
     return img.astype(np.float32)
