@@ -6,7 +6,7 @@ One bench step = one whole decomposition. Metric: Chambolle Mpx*iter/s
 (= H*W*K*n_inner / time / 1e6), whole job over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload config1|m1024|config2|config3] [--extra]
+                  [--workload config1|m1024|config2|config3|config4] [--quick]
 
 Printed: one JSON line on rank 0. `value` is device-timed (inputs resident in HBM, L2
 flushed before every timed step); `e2e` is the same metric through the C ABI with host
@@ -304,18 +304,25 @@ def run_gb300(args):
         result["cpu_baseline"] = {"value": v, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
                                   "sample": f"first {K} of {job.K} ROF steps of the same image ({el:.1f} s)"}
 
-    if args.extra and rank == 0:
-        extra = {}
+    if rank == 0 and not args.quick and args.workload == "config1":
+        # the other two parts of the metric: 1024^2 decompositions/s and served p50/p99,
+        # plus the batched-vs-plain comparison
         m = syn.m1024().jobs[0]
         fm = torch.from_numpy(m.f).to(dev)
         plan.decompose(fm, m.dt, m.K, m.n_inner, m.edges, stream=stream)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         for _ in range(3):
             plan.decompose(fm, m.dt, m.K, m.n_inner, m.edges, stream=stream)
+        e1.record(stream)
         torch.cuda.synchronize()
-        extra["m1024_decomps_per_s"] = 3 / (time.perf_counter() - t0)
-        result["extra"] = extra
+        ms = e0.elapsed_time(e1) / 3
+        result["m1024"] = {"workload": syn.m1024.__doc__.strip().splitlines()[0], "decomps_per_s": 1000.0 / ms,
+                           "ms_per_decomp": ms, "Mpx_iter_per_s": m.px_iters / ms / 1e3}
+        result["batched_config2"] = measure_batched(tv, torch, local, 2, 1)
+        sv = measure_serving(tv, local, [float(args.serve_rate)], args.serve_requests)[0]
+        result["serving_config4"] = {k: v for k, v in sv.items() if k != "clocks"}
 
     if rank == 0:
         print(json.dumps(result))
@@ -325,85 +332,86 @@ def run_gb300(args):
     return 0
 
 
-def run_batched(args, tv, torch, local, ws):
-    """Config 2: 64 images of uneven sizes and schedules. Images/s of the batched path
-    (one set of launches per step over all images, graph-replayed) against the plain path
-    (the same images decomposed one at a time, each graph-replayed), same device buffers."""
+def measure_batched(tv, torch, local, steps: int, warmup: int, with_clocks=None):
+    """Config 2: 64 images of uneven sizes and schedules. Device time of the batched path (one
+    set of launches per step over all images, graph-replayed) against the plain path (the same
+    images decomposed one at a time, each graph-replayed); L2 flushed before every timed step."""
     dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
+    stream = torch.cuda.current_stream(dev)
     wl = syn.config2()
     jobs = [(torch.from_numpy(j.f).to(dev), j.dt, j.K, j.n_inner, j.edges) for j in wl.jobs]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     plan = tv.Plan(local)
+    plain_plan = tv.Plan(local)
 
-    def timed(fn, steps):
+    def timed(fn, n):
         evs = []
-        with ClockSampler(local) as clk:
-            for i in range(steps):
-                flush.fill_(i & 0xff)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                fn()
-                b.record(stream)
-                evs.append((a, b))
-            torch.cuda.synchronize()
-        return sum(x.elapsed_time(y) for x, y in evs) / 1000.0, clk.summary()
+        for i in range(n):
+            flush.fill_(i & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in evs) / 1000.0
 
     batch = lambda: plan.decompose_batch(jobs, stream=stream)
-    for _ in range(args.warmup):
-        batch()
-    torch.cuda.synchronize()
-    s0 = plan.stats()
-    t_batch, clk = timed(batch, args.steps)
-    s1 = plan.stats()
-    plain_plan = tv.Plan(local)
 
     def plain():
         for j in jobs:
             plain_plan.decompose(*j, stream=stream)
 
+    for _ in range(max(1, warmup)):
+        batch()
     plain()
     torch.cuda.synchronize()
-    t_plain, _ = timed(plain, max(1, args.steps // 2))
+    s0 = plan.stats()
+    t_batch = timed(batch, steps)
+    s1 = plan.stats()
+    n_plain = max(1, steps // 2)
+    t_plain = timed(plain, n_plain)
     n_img = len(jobs)
-    px_it = wl.px_iters
-    value = px_it * args.steps / t_batch / 1e6
-    result = {"metric": "Chambolle Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": ws,
-              "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_batch / args.steps,
-              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-              "data": "synthetic",
-              "config": {"workload": wl.name, "images": n_img, "l2": "flushed before every timed step",
-                         "tile": s1["last_tile"], "temporal_block": s1["last_temporal_block"]},
-              "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]), "clocks": clk,
-              "batched": {"images_per_s": n_img * args.steps / t_batch,
-                          "ms_per_batch": 1000 * t_batch / args.steps},
-              "plain_one_at_a_time": {"images_per_s": n_img * max(1, args.steps // 2) / t_plain,
-                                      "ms_per_batch": 1000 * t_plain / max(1, args.steps // 2)}}
-    result["batched_over_plain"] = result["batched"]["images_per_s"] / result["plain_one_at_a_time"]["images_per_s"]
-    print(json.dumps(result))
+    out = {"workload": wl.name, "images": n_img, "px_iters_per_batch": wl.px_iters,
+           "batched_images_per_s": n_img * steps / t_batch, "batched_ms": 1000 * t_batch / steps,
+           "batched_Mpx_iter_per_s": wl.px_iters * steps / t_batch / 1e6,
+           "plain_images_per_s": n_img * n_plain / t_plain, "plain_ms": 1000 * t_plain / n_plain,
+           "tile": s1["last_tile"], "temporal_block": s1["last_temporal_block"],
+           "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"])}
+    out["batched_over_plain"] = out["batched_images_per_s"] / out["plain_images_per_s"]
     plan.close()
     plain_plan.close()
+    return out
+
+
+def run_batched(args, tv, torch, local, ws):
+    dev = torch.device("cuda", local)
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
+    with ClockSampler(local) as clk:
+        m = measure_batched(tv, torch, local, args.steps, args.warmup)
+    result = {"metric": "Chambolle Mpx*iter/s", "value": m["batched_Mpx_iter_per_s"], "unit": "Mpx*iter/s",
+              "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["batched_ms"],
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+              "data": "synthetic",
+              "config": {"workload": m["workload"], "images": m["images"], "l2": "flushed before every timed step",
+                         "tile": m["tile"], "temporal_block": m["temporal_block"]},
+              "gpu_launches": m["gpu_launches"], "clocks": clk.summary(), "batched": m}
+    print(json.dumps(result))
     return 0
 
 
-def run_serving(args, tv, torch, local, ws):
+def measure_serving(tv, local, rates, n_req):
     """Config 4: Poisson arrivals of single-image requests (sizes 256^2..2048^2 with weights
     .4/.3/.2/.1, K ~ U{20..50}, dt .5, 300 iterations, 6 bands) into the serving loop
-    (continuous batching, 60 GiB budget). For each rate: images/s and p50/p99 latency
-    (submit to finish, host clock), and the same requests through the plain path one at a
-    time for images/s. A pool of 8 images per size is reused (timing does not depend on the
-    picture)."""
-    import random
-
-    rates = [float(x) for x in args.rates.split(",")]
-    n_req = args.requests
+    (continuous batching, 60 GiB budget). Per rate: images/s and p50/p99 latency (submit to
+    finish, host clock); the same requests through the plain path one at a time, and as one
+    offline batch, for images/s. A pool of 8 images per size is reused (timing does not
+    depend on the picture)."""
     pool = {}
     for s in (256, 512, 1024, 2048):
         pool[s] = [syn.make_image(s, s, max(1, int(40 * s * s / 512 ** 2)), (2.0, 60.0), (0.05, 1.0), 0.02,
                                   4000 + 10 * s + k) for k in range(8)]
-    out = {"metric": "served images/s and p50/p99 latency", "workload": "config4_serving", "n_gpus": ws,
-           "requests_per_rate": n_req, "data": "synthetic", "load_points": []}
+    points = []
     for rate in rates:
         rng = np.random.default_rng(4000 + int(rate))
         arrivals, jobs = [], []
@@ -416,8 +424,7 @@ def run_serving(args, tv, torch, local, ws):
             jobs.append((pool[s][j % 8], 0.5, K, 300, syn.DYADIC_EDGES))
         px_it = sum(j[0].size * j[2] * j[3] for j in jobs)
         with tv.Plan(local) as plan:
-            # warm the scheduler thread and its tile choice
-            tw, _ = plan.submit(*jobs[0])
+            tw, _ = plan.submit(*jobs[0])  # warm the scheduler thread and its tile choice
             plan.wait(tw)
             plan.serving_stats(reset=True)
             tickets = []
@@ -441,19 +448,27 @@ def run_serving(args, tv, torch, local, ws):
             for job in jobs:
                 plain.decompose(*job)
             t_plain = time.perf_counter() - t1
-            # the same requests as one offline batch: the ceiling of batching them
             plain.decompose_batch(jobs[:4])
             t2 = time.perf_counter()
             plain.decompose_batch(jobs)
             t_batch = time.perf_counter() - t2
-        out["load_points"].append({"rate_req_per_s": rate, "served_images_per_s": n_req / wall,
-                                   "served_Mpx_iter_per_s": px_it / wall / 1e6,
-                                   "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "count": lat["count"],
-                                   "plain_images_per_s": n_req / t_plain,
-                                   "offline_batch_images_per_s": n_req / t_batch,
-                                   "plain_Mpx_iter_per_s": px_it / t_plain / 1e6,
-                                   "offered_duration_s": arrivals[-1], "wall_s": wall, "clocks": clk.summary()})
-        print(json.dumps(out["load_points"][-1]), flush=True)
+        points.append({"rate_req_per_s": rate, "requests": n_req, "served_images_per_s": n_req / wall,
+                       "served_Mpx_iter_per_s": px_it / wall / 1e6,
+                       "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "count": lat["count"],
+                       "plain_images_per_s": n_req / t_plain,
+                       "offline_batch_images_per_s": n_req / t_batch,
+                       "plain_Mpx_iter_per_s": px_it / t_plain / 1e6,
+                       "offered_duration_s": arrivals[-1], "wall_s": wall, "clocks": clk.summary()})
+    return points
+
+
+def run_serving(args, tv, torch, local, ws):
+    rates = [float(x) for x in args.rates.split(",")]
+    out = {"metric": "served images/s and p50/p99 latency", "workload": "config4_serving", "n_gpus": ws,
+           "requests_per_rate": args.requests, "data": "synthetic"}
+    out["load_points"] = measure_serving(tv, local, rates, args.requests)
+    for p in out["load_points"]:
+        print(json.dumps(p), flush=True)
     print(json.dumps(out))
     return 0
 
@@ -506,7 +521,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-k", type=int, default=50, help="ROF steps of the oracle's CPU sample")
     ap.add_argument("--ref-steps-k", type=int, default=6, help="ROF steps per reference-arm step")
-    ap.add_argument("--extra", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the 1024^2, batched and serving summaries of the default run")
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the dual-iteration kernel on a --size x --size image")
     ap.add_argument("--size", type=int, default=4096)
