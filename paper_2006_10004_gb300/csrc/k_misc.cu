@@ -121,19 +121,11 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 //   b^m    += phi_k dt for the band m of t_k; a finished band is written out as float32
 //   f_r     = u_{K-1} - t_{K-1} (u_K - u_{K-1}) / dt at the last step (Eq. finite_inverse_trafo)
 template <typename P>
-__global__ void __launch_bounds__(kEpBlock)
-    k_epilogue(ImgDesc *__restrict__ descs, const int *__restrict__ ep_img,
-               const int *__restrict__ ep_base, int gstep, int depth) {
-    __shared__ double s_red[kEpBlock / 32];
-    __shared__ int s_last;
-    pdl_wait();  // the step's last dual-iteration launch must be complete
-    pdl_trigger();
-    const int b = blockIdx.x;
-    const int img = ep_img[b];
-    ImgDesc *d = descs + img;
+__device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gstep, int depth,
+                                               double *s_red, int &s_last) {
+    const ImgDesc *d = &dd;
     const int k = gstep - d->s0;
     if (k < 0 || k >= d->K) return;  // uniform over the block
-    const int lb = b - ep_base[img];
     const int H = d->H, W = d->W, pitch = d->pitch;
     const int nbx = (W + kEpBlock - 1) / kEpBlock;
     const int i = lb / nbx;
@@ -204,6 +196,30 @@ __global__ void __launch_bounds__(kEpBlock)
     }
 }
 
+template <typename P>
+__global__ void __launch_bounds__(kEpBlock)
+    k_epilogue(ImgDesc *__restrict__ descs, const int *__restrict__ ep_img,
+               const int *__restrict__ ep_base, int gstep, int depth) {
+    __shared__ double s_red[kEpBlock / 32];
+    __shared__ int s_last;
+    pdl_wait();  // the step's last dual-iteration launch must be complete
+    pdl_trigger();
+    const int b = blockIdx.x;
+    const int img = ep_img[b];
+    epilogue_block<P>(descs[img], b - ep_base[img], gstep, depth, s_red, s_last);
+}
+
+// Single-image form: the descriptor is a kernel parameter, block b is local block b.
+template <typename P>
+__global__ void __launch_bounds__(kEpBlock)
+    k_epilogue_one(const __grid_constant__ ImgDesc d, int gstep, int depth) {
+    __shared__ double s_red[kEpBlock / 32];
+    __shared__ int s_last;
+    pdl_wait();
+    pdl_trigger();
+    epilogue_block<P>(d, blockIdx.x, gstep, depth, s_red, s_last);
+}
+
 cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_img,
                             const int *ep_base, int n_blocks, int gstep, int depth,
                             cudaStream_t st, bool pdl) {
@@ -222,6 +238,26 @@ cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_i
         case 0: return cudaLaunchKernelEx(&cfg, k_epilogue<float>, dd, ep_img, ep_base, gstep, depth);
         case 1: return cudaLaunchKernelEx(&cfg, k_epilogue<__half>, dd, ep_img, ep_base, gstep, depth);
         case 2: return cudaLaunchKernelEx(&cfg, k_epilogue<__nv_bfloat16>, dd, ep_img, ep_base, gstep, depth);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_epilogue_one(int p_storage, const ImgDesc &d, int gstep, int depth,
+                                cudaStream_t st, bool pdl) {
+    if (d.ep_blocks <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)d.ep_blocks);
+    cfg.blockDim = dim3(kEpBlock);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    switch (p_storage) {
+        case 0: return cudaLaunchKernelEx(&cfg, k_epilogue_one<float>, d, gstep, depth);
+        case 1: return cudaLaunchKernelEx(&cfg, k_epilogue_one<__half>, d, gstep, depth);
+        case 2: return cudaLaunchKernelEx(&cfg, k_epilogue_one<__nv_bfloat16>, d, gstep, depth);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -122,10 +122,10 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
     }
 }
 
+// One CTA's work on tile (tx, ty) of image d: load, iterate, store the centre.
 template <int V, int R, int RW, int TB, typename P, bool FAST>
-__global__ void __launch_bounds__(32 * RW)
-    k_tiled(const TileRef *__restrict__ tiles, const ImgDesc *__restrict__ descs, int gstep,
-            int blk, int depth, float tau) {
+__device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int gstep, int blk,
+                                           int depth, float tau) {
     static_assert(R * V <= 32, "mask bits");
     static_assert(V % 2 == 0, "pixels are processed in pairs");
     constexpr int VP = V / 2;
@@ -138,27 +138,22 @@ __global__ void __launch_bounds__(32 * RW)
     __shared__ __align__(16) float s_p1b[RW][TW];
     __shared__ __align__(16) float s_wt[RW][TW];
 
-    // nothing below may read what the preceding launch wrote before this point
-    pdl_wait();
-    pdl_trigger();
-    const TileRef t = tiles[blockIdx.x];
-    const ImgDesc *d = descs + t.img;
-    const int H = d->H, W = d->W, pitch = d->pitch;
+    const int H = d.H, W = d.W, pitch = d.pitch;
     // launch blk advances every tile by iterations [blk*depth, min((blk+1)*depth, n_inner));
     // depth <= TB keeps the centre exact
-    const int k = gstep - d->s0;
-    const int n_iter = min(min(depth, TB), d->n_inner - blk * depth);
-    if (k < 0 || k >= d->K || n_iter <= 0) return;  // uniform over the CTA
-    const int src = p_copy(k, launches_per_step(d->n_inner, depth), blk);
-    const P *__restrict__ gp1 = static_cast<const P *>(d->p1[src]);
-    const P *__restrict__ gp2 = static_cast<const P *>(d->p2[src]);
-    P *__restrict__ op1 = static_cast<P *>(d->p1[src ^ 1]);
-    P *__restrict__ op2 = static_cast<P *>(d->p2[src ^ 1]);
-    const float *__restrict__ ggl = d->gl;
+    const int k = gstep - d.s0;
+    const int n_iter = min(min(depth, TB), d.n_inner - blk * depth);
+    if (k < 0 || k >= d.K || n_iter <= 0) return;  // uniform over the CTA
+    const int src = p_copy(k, launches_per_step(d.n_inner, depth), blk);
+    const P *__restrict__ gp1 = static_cast<const P *>(d.p1[src]);
+    const P *__restrict__ gp2 = static_cast<const P *>(d.p2[src]);
+    P *__restrict__ op1 = static_cast<P *>(d.p1[src ^ 1]);
+    P *__restrict__ op2 = static_cast<P *>(d.p2[src ^ 1]);
+    const float *__restrict__ ggl = d.gl;
 
     const int lane = threadIdx.x & 31;
     const int wy = threadIdx.x >> 5;
-    const int x0 = t.tx * OW, y0 = t.ty * OH;
+    const int x0 = tx * OW, y0 = ty * OH;
     const int xs = x0 - HX, ys = y0 - TB;
     const int cx = xs + lane * V;
     const int ry = ys + wy * R;
@@ -239,27 +234,58 @@ __global__ void __launch_bounds__(32 * RW)
     }
 }
 
-// Shape list shared by every storage type; index = tile-shape id of the C ABI.
+// Table form: CTA b works on tiles[b] of image descs[tiles[b].img] (batches of images).
+template <int V, int R, int RW, int TB, int MINB, typename P, bool FAST>
+__global__ void __launch_bounds__(32 * RW, MINB)
+    k_tiled(const TileRef *__restrict__ tiles, const ImgDesc *__restrict__ descs, int gstep,
+            int blk, int depth, float tau) {
+    // nothing below may read what the preceding launch wrote before this point
+    pdl_wait();
+    pdl_trigger();
+    const TileRef t = tiles[blockIdx.x];
+    tiled_tile<V, R, RW, TB, P, FAST>(descs[t.img], t.tx, t.ty, gstep, blk, depth, tau);
+}
+
+// Single-image form: the descriptor travels in the kernel parameters and the tile follows
+// from the block index, so a CTA starts its loads without first reading any table.
+template <int V, int R, int RW, int TB, int MINB, typename P, bool FAST>
+__global__ void __launch_bounds__(32 * RW, MINB)
+    k_tiled_one(const __grid_constant__ ImgDesc d, int ntx, int gstep, int blk, int depth,
+                float tau) {
+    pdl_wait();
+    pdl_trigger();
+    const int b = blockIdx.x;
+    tiled_tile<V, R, RW, TB, P, FAST>(d, b % ntx, b / ntx, gstep, blk, depth, tau);
+}
+
+// Shape list: index (tile-shape id of the C ABI), columns per lane V, rows per thread R, warps
+// RW, most iterations per launch TB, and the minimum CTAs per SM the register budget aims at
+// (0: left to the compiler).
 #define TVSPEC_TILE_SHAPES(X) \
-    X(0, 4, 4, 16, 4)         \
-    X(1, 4, 4, 16, 8)         \
-    X(2, 4, 4, 8, 4)          \
-    X(3, 4, 4, 8, 8)          \
-    X(4, 2, 8, 8, 4)          \
-    X(5, 2, 8, 8, 8)          \
-    X(6, 2, 8, 16, 4)         \
-    X(7, 2, 8, 16, 8)         \
-    X(8, 2, 8, 4, 4)          \
-    X(9, 4, 4, 16, 12)        \
-    X(10, 2, 8, 16, 12)       \
-    X(11, 2, 4, 8, 2)         \
-    X(12, 2, 4, 16, 8)        \
-    X(13, 2, 4, 32, 8)        \
-    X(14, 2, 2, 32, 8)        \
-    X(15, 4, 2, 32, 8)        \
-    X(16, 2, 4, 16, 4)        \
-    X(17, 2, 4, 32, 12)
+    X(0, 4, 4, 16, 4, 0) \
+    X(1, 4, 4, 16, 8, 0) \
+    X(2, 4, 4, 8, 4, 0) \
+    X(3, 4, 4, 8, 8, 0) \
+    X(4, 2, 8, 8, 4, 0) \
+    X(5, 2, 8, 8, 8, 0) \
+    X(6, 2, 8, 16, 4, 0) \
+    X(7, 2, 8, 16, 8, 0) \
+    X(8, 2, 8, 4, 4, 0) \
+    X(9, 4, 4, 16, 12, 0) \
+    X(10, 2, 8, 16, 12, 0) \
+    X(11, 2, 4, 8, 2, 0) \
+    X(12, 2, 4, 16, 8, 0) \
+    X(13, 2, 4, 32, 8, 0) \
+    X(14, 2, 2, 32, 8, 0) \
+    X(15, 4, 2, 32, 8, 0) \
+    X(16, 2, 4, 16, 4, 0) \
+    X(17, 2, 4, 32, 12, 0) \
+    X(18, 2, 8, 8, 8, 3) \
+    X(19, 2, 4, 16, 8, 2) \
+    X(20, 2, 8, 8, 8, 4) \
+    X(21, 2, 4, 8, 8, 4)
 
 using TiledKernel = void (*)(const TileRef *, const ImgDesc *, int, int, int, float);
+using TiledOneKernel = void (*)(const ImgDesc, int, int, int, int, float);
 
 }  // namespace tvspec

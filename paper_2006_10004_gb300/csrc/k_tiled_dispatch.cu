@@ -6,8 +6,9 @@ namespace tvspec {
 TiledKernel tiled_kernel_f32(int shape, bool fast);
 TiledKernel tiled_kernel_f16(int shape, bool fast);
 TiledKernel tiled_kernel_bf16(int shape, bool fast);
+TiledOneKernel tiled_one_kernel_f32(int shape, bool fast);
 
-#define TVSPEC_SHAPE_ROW(idx, V, R, RW, TB) {V, R, RW, TB},
+#define TVSPEC_SHAPE_ROW(idx, V, R, RW, TB, MINB) {V, R, RW, TB},
 static const TileShape kShapes[] = {TVSPEC_TILE_SHAPES(TVSPEC_SHAPE_ROW)};
 #undef TVSPEC_SHAPE_ROW
 
@@ -46,6 +47,28 @@ cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *til
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, k, tiles, descs, gstep, blk, depth, tau);
+}
+
+bool tiled_one_available(int p_storage) { return p_storage == 0; }
+
+cudaError_t launch_tiled_one(int shape, int p_storage, bool fast, const ImgDesc &d, int gstep,
+                             int blk, int depth, float tau, cudaStream_t st, bool pdl) {
+    if (shape < 0 || shape >= tiled_shape_count() || p_storage != 0) return cudaErrorInvalidValue;
+    TiledOneKernel k = tiled_one_kernel_f32(shape, fast);
+    if (!k) return cudaErrorInvalidValue;
+    int ow, oh;
+    tiled_output_tile(kShapes[shape], &ow, &oh);
+    const int ntx = (d.W + ow - 1) / ow, nty = (d.H + oh - 1) / oh;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ntx * nty));
+    cfg.blockDim = dim3((unsigned)(32 * kShapes[shape].RW));
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, d, ntx, gstep, blk, depth, tau);
 }
 
 }  // namespace tvspec

@@ -3,8 +3,8 @@
 
 namespace tvspec {
 
-#define TVSPEC_ENTRY(idx, V, R, RW, TB) \
-    {&k_tiled<V, R, RW, TB, __half, true>, &k_tiled<V, R, RW, TB, __half, false>},
+#define TVSPEC_ENTRY(idx, V, R, RW, TB, MINB) \
+    {&k_tiled<V, R, RW, TB, MINB, __half, true>, &k_tiled<V, R, RW, TB, MINB, __half, false>},
 
 TiledKernel tiled_kernel_f16(int shape, bool fast) {
     static const TiledKernel table[][2] = {TVSPEC_TILE_SHAPES(TVSPEC_ENTRY)};

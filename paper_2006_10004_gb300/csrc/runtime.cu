@@ -425,9 +425,15 @@ static tvspec_status enqueue_iterations(tvspec_plan *plan, LaunchSet &ls,
         nblk = std::max(nblk, launches_per_step(d.n_inner, ls.depth));
     }
     const int nt = ls.tile_prefix[n_active];
+    // one image: its descriptor goes by value, no table reads before the tile loads
+    const bool one = ls.n == 1 && n_active == 1 && tiled_one_available(c.p_storage);
     for (int b = 0; b < nblk; ++b) {
-        cudaError_t e = launch_tiled(ls.shape, c.p_storage, c.fast_math != 0, ls.d_tiles, nt,
-                                     ls.d_descs, gstep, b, ls.depth, c.tau, st, c.pdl != 0);
+        cudaError_t e = one ? launch_tiled_one(ls.shape, c.p_storage, c.fast_math != 0,
+                                               ls.h_descs[0], gstep, b, ls.depth, c.tau, st,
+                                               c.pdl != 0)
+                            : launch_tiled(ls.shape, c.p_storage, c.fast_math != 0, ls.d_tiles,
+                                           nt, ls.d_descs, gstep, b, ls.depth, c.tau, st,
+                                           c.pdl != 0);
         if (e != cudaSuccess) return fail_cuda(e, "tiled kernel launch");
         ++*nk;
     }
@@ -449,9 +455,13 @@ tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *>
     }
     tvspec_status s = enqueue_iterations(plan, ls, slots, n_active, gstep, st, nk);
     if (s != TVSPEC_OK) return s;
-    cudaError_t e = launch_epilogue(c.p_storage, ls.d_descs, ls.d_ep_img, ls.d_ep_base,
-                                    ls.ep_prefix[n_active], gstep, ls.shape < 0 ? 1 : ls.depth, st,
-                                    c.pdl != 0);
+    const int ep_depth = ls.shape < 0 ? 1 : ls.depth;
+    cudaError_t e = (ls.n == 1 && n_active == 1)
+                        ? launch_epilogue_one(c.p_storage, ls.h_descs[0], gstep, ep_depth, st,
+                                              c.pdl != 0)
+                        : launch_epilogue(c.p_storage, ls.d_descs, ls.d_ep_img, ls.d_ep_base,
+                                          ls.ep_prefix[n_active], gstep, ep_depth, st,
+                                          c.pdl != 0);
     if (e != cudaSuccess) return fail_cuda(e, "epilogue launch");
     if (ls.ep_prefix[n_active] > 0) ++*nk;
     return TVSPEC_OK;

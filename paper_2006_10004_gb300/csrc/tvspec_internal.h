@@ -98,6 +98,12 @@ cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *til
                          const ImgDesc *descs, int gstep, int blk, int depth, float tau,
                          cudaStream_t st, bool pdl = false);
 
+// The same pass over the tiles of one image whose descriptor is passed by value (no table
+// reads before the tile loads). Available for p_storage 0 (tiled_one_available).
+bool tiled_one_available(int p_storage);
+cudaError_t launch_tiled_one(int shape, int p_storage, bool fast, const ImgDesc &d, int gstep,
+                             int blk, int depth, float tau, cudaStream_t st, bool pdl = false);
+
 // One iteration per launch over one image (reference GPU kernel): p_in -> p_out.
 cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,
                          void *p1_out, void *p2_out, const float *gl, int H, int W, int pitch,
@@ -118,6 +124,10 @@ cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_b
 cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_img,
                             const int *ep_base, int n_blocks, int gstep, int depth,
                             cudaStream_t st, bool pdl = false);
+
+// The epilogue of one image whose descriptor is passed by value (block b = local block b).
+cudaError_t launch_epilogue_one(int p_storage, const ImgDesc &d, int gstep, int depth,
+                                cudaStream_t st, bool pdl = false);
 
 // One ROF step's primal recovery for the standalone ROF entry: u = g - lambda div p (float32
 // inputs, float32 output, compact layout for u and g, pitched p).
