@@ -76,6 +76,14 @@ typedef struct {
     size_t mem_budget_bytes;/* device memory the serving scheduler may hold; 0 = 60 GiB */
     int max_batch;          /* serving: most requests resident at once; 0 = 256 */
     int pdl;                /* 1: programmatic dependent launch between the kernels of a step; default 0 */
+    int persistent;         /* 1: run a single image's step in one cooperative launch (tiles
+                               resident for the whole step, bounded-wait grid barriers) when all
+                               its tiles fit on the GPU at once; 0 (default): one launch per block
+                               (on GB300 graph-replayed launches are as cheap as the barriers) */
+    int barrier_timeout_ms; /* longest wait at a grid barrier before the kernel gives up and the
+                               call returns TVSPEC_ETIMEOUT; default 2000 */
+    int test_barrier_noshow;/* fault injection for tests: this CTA of the persistent kernel skips
+                               its first barrier, so the others time out; default -1 (off) */
 } tvspec_config;
 
 /* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in

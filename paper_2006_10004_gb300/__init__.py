@@ -41,7 +41,9 @@ class Config(ctypes.Structure):
     _fields_ = [("p_storage", ctypes.c_int), ("warm_start", ctypes.c_int), ("tau", ctypes.c_float),
                 ("kernel", ctypes.c_int), ("tile", ctypes.c_int), ("temporal_block", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("fast_math", ctypes.c_int),
-                ("mem_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("pdl", ctypes.c_int)]
+                ("mem_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("pdl", ctypes.c_int),
+                ("persistent", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
+                ("test_barrier_noshow", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):

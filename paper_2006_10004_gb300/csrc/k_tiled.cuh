@@ -283,7 +283,9 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     X(18, 2, 8, 8, 8, 3) \
     X(19, 2, 4, 16, 8, 2) \
     X(20, 2, 8, 8, 8, 4) \
-    X(21, 2, 4, 8, 8, 4)
+    X(21, 2, 4, 8, 8, 4)         \
+    X(22, 2, 8, 8, 8, 1)         \
+    X(23, 4, 4, 8, 8, 1)
 
 using TiledKernel = void (*)(const TileRef *, const ImgDesc *, int, int, int, float);
 using TiledOneKernel = void (*)(const ImgDesc, int, int, int, int, float);

@@ -427,6 +427,17 @@ static tvspec_status enqueue_iterations(tvspec_plan *plan, LaunchSet &ls,
     const int nt = ls.tile_prefix[n_active];
     // one image: its descriptor goes by value, no table reads before the tile loads
     const bool one = ls.n == 1 && n_active == 1 && tiled_one_available(c.p_storage);
+    if (one && c.persistent && ls.h_descs[0].counter != nullptr && nblk > 1 &&
+        step_coop_fits(ls.shape, c.fast_math != 0, nt)) {
+        // the whole step in one cooperative launch (tiles resident, bounded-wait barriers)
+        cudaError_t e = launch_step_coop(ls.shape, c.fast_math != 0, ls.h_descs[0], gstep,
+                                         ls.depth, c.tau,
+                                         (unsigned long long)c.barrier_timeout_ms * 1000000ull,
+                                         c.test_barrier_noshow, st);
+        if (e != cudaSuccess) return fail_cuda(e, "persistent kernel launch");
+        ++*nk;
+        return TVSPEC_OK;
+    }
     for (int b = 0; b < nblk; ++b) {
         cudaError_t e = one ? launch_tiled_one(ls.shape, c.p_storage, c.fast_math != 0,
                                                ls.h_descs[0], gstep, b, ls.depth, c.tau, st,
@@ -650,9 +661,12 @@ static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStr
     }
     if (mk == TVSPEC_MEM_HOST) {
         TV_CK(cudaStreamSynchronize(st));
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
+            if (E->h_status[i] & kStatusBarrierTimeout)
+                return fail(TVSPEC_ETIMEOUT, "a grid barrier wait ran out (a CTA did not arrive)");
             if (E->h_status[i] & kStatusNonFinite)
                 return fail(TVSPEC_ECUDA, "non-finite value in the flow");
+        }
     }
     plan->decompositions += n;
     return TVSPEC_OK;
@@ -785,6 +799,9 @@ void tvspec_config_init(tvspec_config *cfg) {
     cfg->mem_budget_bytes = 0;
     cfg->max_batch = 0;
     cfg->pdl = 0;
+    cfg->persistent = 0;
+    cfg->barrier_timeout_ms = 2000;
+    cfg->test_barrier_noshow = -1;
 }
 
 tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_plan **out) {
@@ -799,6 +816,7 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
     if (c.temporal_block < 0 || c.temporal_block > 16)
         return fail(TVSPEC_EINVAL, "temporal_block must be in [0, 16]");
     if (c.max_batch < 0) return fail(TVSPEC_EINVAL, "max_batch must be >= 0");
+    if (c.barrier_timeout_ms < 1) return fail(TVSPEC_EINVAL, "barrier_timeout_ms must be >= 1");
     int n_dev = 0;
     cudaError_t e = cudaGetDeviceCount(&n_dev);
     if (e != cudaSuccess || n_dev == 0) {
@@ -956,19 +974,24 @@ tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float
     cudaStream_t st = stream ? (cudaStream_t)stream : plan->stream;
     // copy 1 of the dual field: a plan-owned buffer of the caller's pitched size
     const size_t pb = (size_t)H * pitch * 4;
-    if (plan->ping_bytes < 2 * pb) {
+    const size_t need = 2 * pb + 256;  // + counter, status and barrier words
+    if (plan->ping_bytes < need) {
         TV_CK(cudaStreamSynchronize(st));
         cudaFree(plan->ping);
         plan->ping = nullptr;
         plan->ping_bytes = 0;
-        TV_CK(cudaMalloc(&plan->ping, 2 * pb));
-        plan->ping_bytes = 2 * pb;
+        TV_CK(cudaMalloc(&plan->ping, need));
+        plan->ping_bytes = need;
     }
+    unsigned *words = reinterpret_cast<unsigned *>((char *)plan->ping + 2 * pb);
+    TV_CK(cudaMemsetAsync(words, 0, 16, st));
     ImgDesc d{};
     d.p1[0] = p1;
     d.p2[0] = p2;
     d.p1[1] = plan->ping;
     d.p2[1] = (char *)plan->ping + pb;
+    d.counter = words;
+    d.status = words + 1;
     d.gl = const_cast<float *>(gl);
     d.H = H;
     d.W = W;

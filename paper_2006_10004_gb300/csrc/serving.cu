@@ -116,6 +116,8 @@ static tvspec_status copy_out(cudaStream_t cst, ServeReq &r) {
     unsigned status = 0;
     TV_CK(cudaMemcpyAsync(&status, r.slot.status, sizeof(unsigned), cudaMemcpyDeviceToHost, cst));
     TV_CK(cudaStreamSynchronize(cst));
+    if (status & kStatusBarrierTimeout)
+        return fail(TVSPEC_ETIMEOUT, "a grid barrier wait ran out (a CTA did not arrive)");
     if (status & kStatusNonFinite) return fail(TVSPEC_ECUDA, "non-finite value in the flow");
     return TVSPEC_OK;
 }

@@ -14,6 +14,7 @@ constexpr int kMaxEdges = 65;
 constexpr int kEpBlock = 256;
 // Device status bits written by kernels into ImgDesc::status.
 constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusBarrierTimeout = 2u;  // a bounded grid-barrier wait ran out
 
 // One image of a launch set. Lives in device memory; kernels read it, the epilogue updates
 // the per-image counter and status word.
@@ -31,8 +32,9 @@ struct ImgDesc {
     double *S;              // K-1 output, device
     double *u_trace;        // optional (K+1) H W output, device, or nullptr
     double *partials;       // one partial |phi| sum per epilogue block
-    unsigned *counter;      // epilogue blocks finished in the current step
-    unsigned *status;       // device status bits
+    unsigned *counter;      // epilogue blocks finished in the current step; counter[2..3]
+                            // hold the persistent kernel's grid barrier (arrivals, generation)
+    unsigned *status;       // device status bits (counter + 1)
     const signed char *band_of_k;  // K entries: band of t_k (host-decided in float64), -1 none
     int H, W, pitch;
     int K, n_inner;
@@ -103,6 +105,13 @@ cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *til
 bool tiled_one_available(int p_storage);
 cudaError_t launch_tiled_one(int shape, int p_storage, bool fast, const ImgDesc &d, int gstep,
                              int blk, int depth, float tau, cudaStream_t st, bool pdl = false);
+
+// Persistent form: all of a step's dual iterations for one image in one cooperative launch
+// (fp32 storage). step_coop_fits says whether all tiles can be resident at once.
+bool step_coop_fits(int shape, bool fast, int n_tiles);
+cudaError_t launch_step_coop(int shape, bool fast, const ImgDesc &d, int gstep, int depth,
+                             float tau, unsigned long long timeout_ns, int noshow_block,
+                             cudaStream_t st);
 
 // One iteration per launch over one image (reference GPU kernel): p_in -> p_out.
 cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,

@@ -140,6 +140,30 @@ def test_programmatic_dependent_launch_bit_identical(tv):
         _same(a.decompose(*args, trace=True), b.decompose(*args, trace=True))
 
 
+def test_persistent_step_kernel_bit_identical(tv):
+    # one cooperative launch per step (tiles resident, grid barriers) vs one launch per block
+    for H, W in [(256, 300), (512, 512), (37, 53)]:
+        f = _img(H, W, 11 + H)
+        args = (f, 0.5, 4, 41, syn.DYADIC_EDGES)
+        with tv.Plan(0, persistent=1) as a, tv.Plan(0, persistent=0) as b:
+            _same(a.decompose(*args, trace=True), b.decompose(*args, trace=True))
+
+
+def test_persistent_barrier_timeout_is_reported_and_plan_recovers(tv):
+    # fault injection on the host side of the contract: one CTA never arrives at its barrier,
+    # the others give up after the bounded wait and the call reports TVSPEC_ETIMEOUT; the
+    # device stays usable
+    f = _img(200, 200, 12)
+    with tv.Plan(0, persistent=1, barrier_timeout_ms=20, test_barrier_noshow=0) as p:
+        with pytest.raises(tv.TvSpecError) as ei:
+            p.decompose(f, 0.5, 3, 30, syn.DYADIC_EDGES)
+        assert ei.value.status == tv.ETIMEOUT
+    with tv.Plan(0) as p:
+        out = p.decompose(f, 0.5, 3, 30, syn.DYADIC_EDGES)
+    ref = oracle.decompose(f, 0.5, 3, 30, syn.DYADIC_EDGES)
+    assert_parity(out, ref, f, "after timeout")
+
+
 def test_device_and_host_memory_bit_identical(plan):
     import torch
 
