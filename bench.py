@@ -321,6 +321,7 @@ def run_gb300(args):
         result["m1024"] = {"workload": syn.m1024.__doc__.strip().splitlines()[0], "decomps_per_s": 1000.0 / ms,
                            "ms_per_decomp": ms, "Mpx_iter_per_s": m.px_iters / ms / 1e3}
         result["batched_config2"] = measure_batched(tv, torch, local, 2, 1)
+        result["training_crops"] = measure_crops(tv, torch, local)
         sv = measure_serving(tv, local, [float(args.serve_rate)], args.serve_requests)[0]
         result["serving_config4"] = {k: v for k, v in sv.items() if k != "clocks"}
 
@@ -381,6 +382,32 @@ def measure_batched(tv, torch, local, steps: int, warmup: int, with_clocks=None)
     out["batched_over_plain"] = out["batched_images_per_s"] / out["plain_images_per_s"]
     plan.close()
     plain_plan.close()
+    return out
+
+
+def measure_crops(tv, torch, local, n: int = 3000):
+    """The paper's ground-truth generation use (Sec. 4.1): many 64x64 greyscale crops, K = 50
+    steps of dt = 0.5, 300 iterations, 6 dyadic bands, as one batch. Device time of the
+    resident path (one CTA per image, one launch) against the per-step path."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    crops = [torch.from_numpy(syn.make_image(64, 64, 6, (3.0, 16.0), (0.1, 1.0), 0.01, 9000 + j)).to(dev)
+             for j in range(n)]
+    jobs = [(c, 0.5, 50, 300, syn.DYADIC_EDGES) for c in crops]
+    out = {"workload": f"{n} crops 64x64, K=50, dt=.5, 300 iterations, 6 dyadic bands"}
+    for name, res in (("resident", 1), ("per_step", 0)):
+        with tv.Plan(local, resident=res) as p:
+            p.decompose_batch(jobs, stream=stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.decompose_batch(jobs, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"images_per_s": n / ms * 1e3, "ms": ms,
+                         "Mpx_iter_per_s": n * 64 * 64 * 50 * 300 / ms / 1e3}
+    out["resident_over_per_step"] = out["resident"]["images_per_s"] / out["per_step"]["images_per_s"]
     return out
 
 

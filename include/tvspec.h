@@ -84,6 +84,11 @@ typedef struct {
                                call returns TVSPEC_ETIMEOUT; default 2000 */
     int test_barrier_noshow;/* fault injection for tests: this CTA of the persistent kernel skips
                                its first barrier, so the others time out; default -1 (off) */
+    int resident;           /* images up to 64x128 or 128x64 can run their whole decomposition
+                               in one CTA (one launch for all of them): 1 (default) when a call
+                               holds at least 32 such images (one CTA per image needs many images
+                               to fill the GPU), 2 always, 0 never; with kernel = AUTO and fp32
+                               storage of p */
 } tvspec_config;
 
 /* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in

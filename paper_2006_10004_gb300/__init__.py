@@ -43,7 +43,7 @@ class Config(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("fast_math", ctypes.c_int),
                 ("mem_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("pdl", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
-                ("test_barrier_noshow", ctypes.c_int)]
+                ("test_barrier_noshow", ctypes.c_int), ("resident", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):

@@ -1,6 +1,7 @@
 // Kernels around the hot loop: the reference one-iteration kernel, the start of a
 // decomposition, the per-step float64 epilogue and the standalone ROF helpers.
 #include "chambolle_math.cuh"
+#include "epilogue.cuh"
 #include "tvspec_internal.h"
 
 namespace tvspec {
@@ -95,24 +96,6 @@ cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_b
     return cudaGetLastError();
 }
 
-// Fixed-order block sum of a double (warp shuffle tree, then the first warp over the warps).
-__device__ __forceinline__ double block_sum(double v, double *s_red) {
-    constexpr unsigned FULL = 0xffffffffu;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (warp == 0) {
-        t = (lane < (int)(blockDim.x >> 5)) ? s_red[lane] : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(FULL, t, off);
-    }
-    __syncthreads();
-    return t;  // valid in thread 0
-}
-
 // One step's epilogue, per pixel, all in float64 (Sec. 2.1-2.2):
 //   u_{k+1} = u_k - dt div p                 (Chambolle's primal recovery of the ROF step)
 //   gl      = u_{k+1} / dt                    (data term of the next step's dual iterations)
@@ -130,7 +113,6 @@ __device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gs
     const int nbx = (W + kEpBlock - 1) / kEpBlock;
     const int i = lb / nbx;
     const int j = (lb % nbx) * kEpBlock + threadIdx.x;
-    const size_t N = (size_t)H * W;
     double absphi = 0.0;
     if (j < W) {
         // the copy of p written by the step's last launch
@@ -138,41 +120,12 @@ __device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gs
         const P *p1 = static_cast<const P *>(d->p1[cp]);
         const P *p2 = static_cast<const P *>(d->p2[cp]);
         const size_t o = (size_t)i * pitch + j;
-        const size_t n = (size_t)i * W + j;
-        // div p with the adjoint boundary terms (negative adjoint of the forward gradient)
-        const double a = (i < H - 1 ? (double)PStore<P>::load(p1[o]) : 0.0) -
-                         (i > 0 ? (double)PStore<P>::load(p1[o - pitch]) : 0.0);
-        const double c = (j < W - 1 ? (double)PStore<P>::load(p2[o]) : 0.0) -
-                         (j > 0 ? (double)PStore<P>::load(p2[o - 1]) : 0.0);
-        double *ucur = (k & 1) ? d->ub : d->ua;
-        double *uoth = (k & 1) ? d->ua : d->ub;  // u_{k-1} in, u_{k+1} out
-        const double uc = ucur[n];
-        const double un = uc - d->dt * (a + c);
-        if (!isfinite(un)) atomicOr(d->status, kStatusNonFinite);
-        d->gl[o] = (float)(un * d->inv_dt);
-        if (d->u_trace) d->u_trace[(size_t)(k + 1) * N + n] = un;
-        if (k >= 1) {
-            const double up = uoth[n];
-            const double tk = (double)k * d->dt;
-            const double phi = tk * (un - 2.0 * uc + up) * (d->inv_dt * d->inv_dt);
-            absphi = fabs(phi);
-            const int m = d->band_of_k[k];
-            const int mp = (k >= 2) ? d->band_of_k[k - 1] : -1;
-            double acc = 0.0;
-            if (mp >= 0) {
-                const double old = d->acc[n];
-                if (mp == m) acc = old;
-                else d->bands[(size_t)mp * N + n] = (float)old;  // band mp is complete
-            }
-            if (m >= 0) acc += phi * d->dt;
-            if (k == d->K - 1) {
-                if (m >= 0) d->bands[(size_t)m * N + n] = (float)acc;
-                d->residual[n] = (float)(uc - tk * (un - uc) * d->inv_dt);
-            } else {
-                d->acc[n] = acc;
-            }
-        }
-        uoth[n] = un;
+        const double divp =
+            div_at(i, j, H, W, PStore<P>::load(p1[o]), i > 0 ? PStore<P>::load(p1[o - pitch]) : 0.0f,
+                   PStore<P>::load(p2[o]), j > 0 ? PStore<P>::load(p2[o - 1]) : 0.0f);
+        float gl_next;
+        absphi = epilogue_pixel(*d, k, (size_t)i * W + j, divp, &gl_next);
+        d->gl[o] = gl_next;
     }
     if (k < 1) return;  // no phi at step 0
     const double bsum = block_sum(absphi, s_red);

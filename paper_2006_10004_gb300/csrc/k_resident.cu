@@ -1,0 +1,214 @@
+// Resident kernel for small images: one CTA runs a whole decomposition -- u_0 = f, then K
+// steps of n_inner dual iterations and the float64 epilogue -- for an image that fits the
+// CTA's register tile (W <= 32 V, H <= RW R), in one launch for a whole batch of such images.
+//
+// The tile is the image itself, so there is no halo and no exchange with other CTAs: the
+// tiled kernel's iteration (tiled_iterate, with the border masks) runs n_inner times per step
+// in registers. For the epilogue the CTA writes p to global memory (L2) once per step, reads
+// the divergence neighbours back after a CTA barrier, and applies the shared per-pixel
+// epilogue (epilogue_pixel). S(t_k) is reduced with the same partition (one 256-wide block per
+// image row) and the same shuffle trees as the multi-block epilogue, so every output is
+// bit-identical to the multi-launch path.
+#include "epilogue.cuh"
+#include "k_tiled.cuh"
+
+namespace tvspec {
+
+template <int V, int R, int RW, bool FAST>
+__global__ void __launch_bounds__(32 * RW, 1)
+    k_resident(const ImgDesc *__restrict__ descs, const int *__restrict__ idx, float tau,
+               int warm_start) {
+    static_assert(RW % 8 == 0, "the S reduction works in groups of 8 warps");
+    constexpr int VP = V / 2;
+    constexpr int TW = 32 * V;
+    constexpr int TH = RW * R;
+    constexpr int NG = RW / 8;  // groups of 256 threads
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ __align__(16) float s_p1b[RW][TW];
+    __shared__ __align__(16) float s_wt[RW][TW];
+    __shared__ double s_red[NG][8];
+    __shared__ double s_part[TH];
+    extern __shared__ double s_phi[];  // H * W values of |phi_k|
+
+    const ImgDesc &d = descs[idx[blockIdx.x]];
+    const int H = d.H, W = d.W, pitch = d.pitch;
+    const int lane = threadIdx.x & 31;
+    const int wy = threadIdx.x >> 5;
+    const int cx = lane * V;
+    const int ry = wy * R;
+    float *gp1 = static_cast<float *>(d.p1[0]);
+    float *gp2 = static_cast<float *>(d.p2[0]);
+
+    // border masks: the tile is the image, every tile pixel outside it stays zero
+    unsigned m1 = 0u, m2 = 0u;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = ry + r;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int c = cx + v;
+            if (y < H - 1 && c < W) m1 |= 1u << (r * V + v);
+            if (y < H && c < W - 1) m2 |= 1u << (r * V + v);
+        }
+    }
+
+    // u_0 = f (Eq. TVflow), g/dt of step 0, p = 0
+    float2 p1[R][VP], p2[R][VP], gl[R][VP];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int j = 0; j < VP; ++j) {
+            p1[r][j] = p2[r][j] = gl[r][j] = make_float2(0.0f, 0.0f);
+            float g2[2] = {0.0f, 0.0f};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int y = ry + r, c = cx + 2 * j + h;
+                if (y < H && c < W) {
+                    const size_t n = (size_t)y * W + c;
+                    const float fv = d.f[n];
+                    if (!isfinite(fv)) atomicOr(d.status, kStatusNonFinite);
+                    const double u0 = (double)fv;
+                    d.ua[n] = u0;
+                    if (d.u_trace) d.u_trace[n] = u0;
+                    g2[h] = (float)(u0 * d.inv_dt);
+                }
+            }
+            gl[r][j] = make_float2(g2[0], g2[1]);
+        }
+    }
+
+    for (int k = 0; k < d.K; ++k) {
+        if (!warm_start) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int j = 0; j < VP; ++j) p1[r][j] = p2[r][j] = make_float2(0.0f, 0.0f);
+        }
+        if (RW > 1) {
+            FPack<V> q;
+#pragma unroll
+            for (int j = 0; j < VP; ++j) {
+                q.v[2 * j] = p1[R - 1][j].x;
+                q.v[2 * j + 1] = p1[R - 1][j].y;
+            }
+            *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
+        }
+        __syncthreads();
+        tiled_iterate<V, R, RW, FAST, true, true>(p1, p2, gl, d.n_inner, tau, m1, m2, s_p1b,
+                                                  s_wt, lane, wy);
+        // p to global for the divergence's neighbours
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = ry + r;
+            if (y < H && cx < W) {
+                FPack<V> a, b;
+#pragma unroll
+                for (int j = 0; j < VP; ++j) {
+                    a.v[2 * j] = p1[r][j].x;
+                    a.v[2 * j + 1] = p1[r][j].y;
+                    b.v[2 * j] = p2[r][j].x;
+                    b.v[2 * j + 1] = p2[r][j].y;
+                }
+                *reinterpret_cast<FPack<V> *>(gp1 + (size_t)y * pitch + cx) = a;
+                *reinterpret_cast<FPack<V> *>(gp2 + (size_t)y * pitch + cx) = b;
+            }
+        }
+        __syncthreads();
+        // the epilogue on every own pixel
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int j = 0; j < VP; ++j) {
+                float g2[2] = {gl[r][j].x, gl[r][j].y};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int y = ry + r, c = cx + 2 * j + h;
+                    if (y < H && c < W) {
+                        const size_t o = (size_t)y * pitch + c;
+                        const float pv1 = h == 0 ? p1[r][j].x : p1[r][j].y;
+                        const float pv2 = h == 0 ? p2[r][j].x : p2[r][j].y;
+                        const double divp = div_at(y, c, H, W, pv1, y > 0 ? gp1[o - pitch] : 0.0f,
+                                                   pv2, c > 0 ? gp2[o - 1] : 0.0f);
+                        const double a = epilogue_pixel(d, k, (size_t)y * W + c, divp, &g2[h]);
+                        s_phi[(size_t)y * W + c] = a;
+                    }
+                }
+                gl[r][j] = make_float2(g2[0], g2[1]);
+            }
+        }
+        __syncthreads();
+        if (k >= 1) {
+            // S(t_k) exactly as the multi-block epilogue sums it: one 256-wide block per row
+            // (thread t holds column t, zero past W), then the row sums in one block
+            const int g = threadIdx.x >> 8;
+            const int t = threadIdx.x & 255;
+            const int wg = t >> 5;
+            for (int i0 = 0; i0 < H; i0 += NG) {
+                const int i = i0 + g;
+                double v = (i < H && t < W) ? s_phi[(size_t)i * W + t] : 0.0;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+                if (lane == 0) s_red[g][wg] = v;
+                __syncthreads();
+                if (wg == 0) {
+                    double x = lane < 8 ? s_red[g][lane] : 0.0;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULL, x, off);
+                    if (lane == 0 && i < H) s_part[i] = x;
+                }
+                __syncthreads();
+            }
+            if (g == 0) {
+                double v = 0.0;
+                if (t < H) v += s_part[t];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+                if (lane == 0) s_red[0][wg] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                double x = lane < 8 ? s_red[0][lane] : 0.0;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULL, x, off);
+                if (lane == 0) d.S[k - 1] = x;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Variants: (V, R, RW) -> image tile (32 V) x (RW R).
+using ResidentKernel = void (*)(const ImgDesc *, const int *, float, int);
+
+struct ResidentVariant {
+    int V, R, RW;
+    ResidentKernel fast, ieee;
+};
+
+static const ResidentVariant kResident[] = {
+    {2, 2, 32, &k_resident<2, 2, 32, true>, &k_resident<2, 2, 32, false>},  //  64 x  64
+    {2, 4, 32, &k_resident<2, 4, 32, true>, &k_resident<2, 4, 32, false>},  //  64 x 128
+    {4, 2, 32, &k_resident<4, 2, 32, true>, &k_resident<4, 2, 32, false>},  // 128 x  64
+};
+
+int resident_variant_for(int H, int W) {
+    for (int i = 0; i < (int)(sizeof(kResident) / sizeof(kResident[0])); ++i)
+        if (W <= 32 * kResident[i].V && H <= kResident[i].RW * kResident[i].R && W <= 256 &&
+            H <= 256)
+            return i;
+    return -1;
+}
+
+cudaError_t launch_resident(int variant, bool fast, const ImgDesc *descs, const int *idx, int n,
+                            float tau, int warm_start, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const ResidentVariant &v = kResident[variant];
+    const ResidentKernel k = fast ? v.fast : v.ieee;
+    const size_t smem = (size_t)(32 * v.V) * (v.RW * v.R) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<n, 32 * v.RW, smem, st>>>(descs, idx, tau, warm_start);
+    return cudaGetLastError();
+}
+
+}  // namespace tvspec

@@ -37,7 +37,9 @@ struct alignas(sizeof(float) * V) FPack {
 
 // The iterations of one launch on the registers of one thread. Pixels are processed in
 // horizontal pairs (columns 2q, 2q+1 of the lane) with packed f32x2 arithmetic.
-template <int V, int R, int RW, bool FAST, bool EDGE>
+// ZERO_LEFT: the tile's first column is the image's first column (no halo), so lane 0's left
+// neighbour p2_{i,-1} is 0 rather than a halo value.
+template <int V, int R, int RW, bool FAST, bool EDGE, bool ZERO_LEFT = false>
 __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
                                               const float2 (&gl)[R][V / 2], int n_iter,
                                               float tau, unsigned m1bits, unsigned m2bits,
@@ -59,7 +61,8 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float left0 = __shfl_up_sync(FULL, p2[r][VP - 1].y, 1);
+            float left0 = __shfl_up_sync(FULL, p2[r][VP - 1].y, 1);
+            if (ZERO_LEFT && lane == 0) left0 = 0.0f;
 #pragma unroll
             for (int j = 0; j < VP; ++j) {
                 const float2 p1u = (r == 0) ? up[j] : p1[r - 1][j];

@@ -23,6 +23,8 @@ tvspec_status fail_cuda(cudaError_t e, const char *what) {
 }
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+// resident = 1 uses the one-CTA-per-image kernel from this many eligible images on
+constexpr int kResidentMinBatch = 32;
 static int storage_bytes(int s) { return s == 0 ? 4 : 2; }
 static int pitch_for(int W) { return (W + 3) / 4 * 4; }
 static int ep_blocks_for(int H, int W) { return H * ((W + kEpBlock - 1) / kEpBlock); }
@@ -484,13 +486,25 @@ static tvspec_status enqueue_decomposition(tvspec_plan *plan, CacheEntry &E, cud
     std::vector<Slot *> sp;
     for (Slot &s : E.slots) sp.push_back(&s);
     for (Slot &s : E.slots) TV_CK(cudaMemsetAsync(s.base + s.zero_off, 0, s.zero_bytes, st));
+    // resident images: their whole decomposition, one launch per variant
+    int off = 0;
+    for (auto &g : E.res_groups) {
+        cudaError_t e = launch_resident(g.first, plan->cfg.fast_math != 0, E.ls.d_descs,
+                                        E.d_res_idx + off, g.second, plan->cfg.tau,
+                                        plan->cfg.warm_start, st);
+        if (e != cudaSuccess) return fail_cuda(e, "resident kernel launch");
+        ++*nk;
+        off += g.second;
+    }
+    if (E.n_tiled == 0) return TVSPEC_OK;
     cudaError_t e = launch_init(E.ls.d_descs, E.ls.d_ep_img, E.ls.d_ep_base,
-                                E.ls.ep_prefix[E.ls.n], st);
+                                E.ls.ep_prefix[E.n_tiled], st);
     if (e != cudaSuccess) return fail_cuda(e, "init launch");
     ++*nk;
     for (int g = 0; g < E.maxK; ++g) {
         int n_active = 0;
-        while (n_active < (int)E.slots.size() && E.slots[n_active].K > g) ++n_active;
+        while (n_active < E.n_tiled && E.slots[n_active].K > g) ++n_active;
+        if (n_active == 0) break;
         tvspec_status s = enqueue_step(plan, E.ls, sp, n_active, g, st, nk);
         if (s != TVSPEC_OK) return s;
     }
@@ -505,6 +519,8 @@ static void free_entry(CacheEntry &E, cudaStream_t st) {
     for (Slot &s : E.slots) slot_free(&s, st);
     E.slots.clear();
     E.ls.release();
+    cudaFree(E.d_res_idx);
+    E.d_res_idx = nullptr;
     if (E.h_status) cudaFreeHost(E.h_status);
     E.h_status = nullptr;
 }
@@ -541,10 +557,31 @@ static tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs,
     auto E = std::make_unique<CacheEntry>();
     E->key = key;
     const int n = (int)jobs.size();
+    const tvspec_config &cf = plan->cfg;
+    const bool resident_ok = cf.resident && cf.p_storage == TVSPEC_P_FP32 &&
+                             (cf.kernel == TVSPEC_KERNEL_AUTO ||
+                              (cf.kernel == TVSPEC_KERNEL_TILED && cf.tile < 0 && cf.temporal_block == 0));
+    std::vector<int> variant(n, -1);
+    if (resident_ok) {
+        int eligible = 0;
+        for (int i = 0; i < n; ++i) {
+            variant[i] = resident_variant_for(jobs[i].r.H, jobs[i].r.W);
+            eligible += variant[i] >= 0;
+        }
+        // one CTA per image only pays off when there are enough images to fill the GPU
+        if (cf.resident == 1 && eligible < kResidentMinBatch) variant.assign(n, -1);
+    }
+    // tiled images first, by K descending (the images still running at a step are a prefix),
+    // then the resident ones grouped by variant
     E->order.resize(n);
     for (int i = 0; i < n; ++i) E->order[i] = i;
-    std::stable_sort(E->order.begin(), E->order.end(),
-                     [&](int a, int b) { return jobs[a].r.K > jobs[b].r.K; });
+    std::stable_sort(E->order.begin(), E->order.end(), [&](int a, int b) {
+        if ((variant[a] >= 0) != (variant[b] >= 0)) return variant[a] < 0;
+        if (variant[a] >= 0) return variant[a] < variant[b];
+        return jobs[a].r.K > jobs[b].r.K;
+    });
+    E->n_tiled = 0;
+    while (E->n_tiled < n && variant[E->order[E->n_tiled]] < 0) ++E->n_tiled;
     const bool naive = plan->cfg.kernel == TVSPEC_KERNEL_NAIVE;
     if (naive && n != 1) return fail(TVSPEC_ENOTSUP, "the reference kernel runs one image at a time");
     for (int i = 0; i < n; ++i) {
@@ -560,12 +597,29 @@ static tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs,
     }
     TV_CK(cudaStreamSynchronize(plan->stream));
     std::vector<Slot *> sp;
-    for (Slot &s : E->slots) sp.push_back(&s);
+    for (int i = 0; i < E->n_tiled; ++i) sp.push_back(&E->slots[i]);
     int shape = -1, depth = 1;
-    tvspec_status st = choose_tiles(plan, sp, plan->stream, &shape, &depth);
+    tvspec_status st = TVSPEC_OK;
+    if (!sp.empty()) st = choose_tiles(plan, sp, plan->stream, &shape, &depth);
+    else if (plan->cfg.kernel != TVSPEC_KERNEL_NAIVE) shape = 0, depth = 1;
     if (st != TVSPEC_OK) {
         free_entry(*E, plan->stream);
         return st;
+    }
+    if (E->n_tiled < n) {
+        std::vector<int> idx;
+        for (int i = E->n_tiled; i < n; ++i) {
+            const int v = variant[E->order[i]];
+            if (E->res_groups.empty() || E->res_groups.back().first != v) E->res_groups.push_back({v, 0});
+            E->res_groups.back().second++;
+            idx.push_back(i);
+        }
+        size_t cap = 0;
+        st = grow_upload(&E->d_res_idx, &cap, idx);
+        if (st != TVSPEC_OK) {
+            free_entry(*E, plan->stream);
+            return st;
+        }
     }
     std::vector<ImgDesc> descs;
     for (Slot &s : E->slots) descs.push_back(slot_desc(s, 0));
@@ -802,6 +856,7 @@ void tvspec_config_init(tvspec_config *cfg) {
     cfg->persistent = 0;
     cfg->barrier_timeout_ms = 2000;
     cfg->test_barrier_noshow = -1;
+    cfg->resident = 1;
 }
 
 tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_plan **out) {
@@ -817,6 +872,7 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
         return fail(TVSPEC_EINVAL, "temporal_block must be in [0, 16]");
     if (c.max_batch < 0) return fail(TVSPEC_EINVAL, "max_batch must be >= 0");
     if (c.barrier_timeout_ms < 1) return fail(TVSPEC_EINVAL, "barrier_timeout_ms must be >= 1");
+    if (c.resident < 0 || c.resident > 2) return fail(TVSPEC_EINVAL, "resident must be 0, 1 or 2");
     int n_dev = 0;
     cudaError_t e = cudaGetDeviceCount(&n_dev);
     if (e != cudaSuccess || n_dev == 0) {

@@ -83,7 +83,10 @@ void tiles_for(int shape, int H, int W, int *ntx, int *nty);
 
 struct CacheEntry {
     std::string key;
-    std::vector<Slot> slots;     // in run order (sorted by K, descending)
+    std::vector<Slot> slots;     // run order: tiled images by K (descending), then resident ones
+    int n_tiled = 0;             // slots [0, n_tiled) run step by step, the rest resident
+    int *d_res_idx = nullptr;    // slot indices of resident images, grouped by variant
+    std::vector<std::pair<int, int>> res_groups;  // (variant, count) in d_res_idx order
     std::vector<int> order;      // order[i] = index of the caller's request in slot i
     LaunchSet ls;
     int maxK = 0;

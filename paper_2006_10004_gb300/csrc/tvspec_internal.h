@@ -113,6 +113,12 @@ cudaError_t launch_step_coop(int shape, bool fast, const ImgDesc &d, int gstep, 
                              float tau, unsigned long long timeout_ns, int noshow_block,
                              cudaStream_t st);
 
+// Resident small-image kernel: the whole decomposition of each image idx[0..n) of descs in
+// one CTA (fp32). resident_variant_for gives the variant whose tile holds an H x W image, or -1.
+int resident_variant_for(int H, int W);
+cudaError_t launch_resident(int variant, bool fast, const ImgDesc *descs, const int *idx, int n,
+                            float tau, int warm_start, cudaStream_t st);
+
 // One iteration per launch over one image (reference GPU kernel): p_in -> p_out.
 cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,
                          void *p1_out, void *p2_out, const float *gl, int H, int W, int pitch,

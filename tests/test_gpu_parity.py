@@ -140,6 +140,35 @@ def test_programmatic_dependent_launch_bit_identical(tv):
         _same(a.decompose(*args, trace=True), b.decompose(*args, trace=True))
 
 
+@pytest.mark.parametrize("H,W", [(64, 64), (1, 1), (1, 17), (19, 1), (37, 53), (100, 37), (40, 70),
+                                 (64, 128), (128, 64), (63, 127)])
+@pytest.mark.parametrize("warm", [1, 0])
+def test_resident_small_image_kernel_bit_identical(tv, H, W, warm):
+    # the whole decomposition in one CTA vs one launch per block and step
+    f = _img(H, W, 7 * H + W)
+    args = (f, 0.5, 6, 27, syn.DYADIC_EDGES)
+    with tv.Plan(0, resident=2, warm_start=warm) as a, tv.Plan(0, resident=0, warm_start=warm) as b:
+        ra = a.decompose(*args, trace=True)
+        assert a.stats()["kernel_launches"] == 1  # one launch for the whole decomposition
+        _same(ra, b.decompose(*args, trace=True))
+    ref = oracle.decompose(*args, trace=True, warm_start=bool(warm))
+    assert_parity(ra, ref, f, f"resident {H}x{W}")
+
+
+def test_resident_batch_of_crops(tv):
+    # the training-data use: many 64^2 crops, K = 50, dyadic bands, in one launch (the default
+    # chooses the resident kernel from 32 eligible images on)
+    jobs = [(_img(64, 64, 300 + j), 0.5, 50, 60, syn.DYADIC_EDGES) for j in range(40)]
+    with tv.Plan(0) as p:
+        outs = p.decompose_batch(jobs)
+        assert p.stats()["kernel_launches"] == 1
+    with tv.Plan(0) as p:
+        p.decompose_batch(jobs[:8])
+        assert p.stats()["kernel_launches"] > 1  # too few images: per-step path
+    for job, out in zip(jobs[:3], outs[:3]):
+        assert_parity(out, oracle.decompose(*job), job[0], "crop")
+
+
 def test_persistent_step_kernel_bit_identical(tv):
     # one cooperative launch per step (tiles resident, grid barriers) vs one launch per block
     for H, W in [(256, 300), (512, 512), (37, 53)]:
