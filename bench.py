@@ -37,6 +37,18 @@ import synthetic as syn  # noqa: E402
 ALG_BYTES_FP32 = 20  # read p (8) + read g/lambda (4) + write p (8) per pixel per iteration
 
 
+def kernel_source_hash() -> str:
+    """Hash of the dual-iteration kernel's sources: DRAM traffic recorded from an ncu capture
+    (profiles/traffic.json) is only reported while the kernel is unchanged since the capture."""
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in ("k_tiled.cuh", "chambolle_math.cuh"):
+        with open(os.path.join(ROOT, "paper_2006_10004_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -183,7 +195,7 @@ def run_gb300(args):
     if args.workload == "config4":
         return run_serving(args, tv, torch, local, ws)
     wl = _workload(args.workload)
-    plan = tv.Plan(local)
+    plan = tv.Plan(local, **({"kernel": tv.KERNEL_TILED, "tile": args.tile} if args.tile >= 0 else {}))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -288,7 +300,8 @@ def run_gb300(args):
         tf = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tf):
             try:
-                traffic = json.load(open(tf)).get(f"{wl.name}/tile{s1['last_tile']}/tb{depth}")
+                key = f"{wl.name}/tile{s1['last_tile']}/tb{depth}/{kernel_source_hash()}"
+                traffic = json.load(open(tf)).get(key)
             except Exception:
                 traffic = None
         result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -556,7 +569,9 @@ def main():
                     help="time only the dual-iteration kernel on a --size x --size image")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--launches", type=int, default=6)
-    ap.add_argument("--tile", type=int, default=-1, help="--kernel-only: fixed tile shape (-1 = autotune)")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="fixed tile shape of the dual-iteration kernel (-1 = autotune), e.g. to pin the "
+                         "autotuner's choice under a profiler")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
