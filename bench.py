@@ -133,6 +133,26 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate_over_ranks(t_sec: float, units: float, dist=None):
+    """Whole-job throughput of weak-scaled replicas: every rank processed `units` (pixel-
+    iterations) in `t_sec` seconds of device time; the job's time is the slowest rank's, and
+    the value is all ranks' units over it. With dist (torch.distributed, any backend) the
+    ranks synchronise on a barrier and agree on the maximum; returns (value, t_max)."""
+    import torch
+
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return units / t_sec, t_sec
+    ws = dist.get_world_size()
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    dist.barrier()
+    t = torch.tensor([t_sec], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    t_max = float(t.item())
+    return float(u.item()) / t_max, t_max
+
+
 def _oracle_sample(job, max_k: int):
     """FP64 oracle on a bounded sample of the job: the first max_k ROF steps of the same image."""
     import oracle
@@ -235,12 +255,8 @@ def run_gb300(args):
         pg.barrier()
     st1 = plan.stats()
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t_sec = dev_ms / 1000.0
-    if pg:
-        t = torch.tensor([t_sec], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_sec = float(t.item())
-    value = px_it * args.steps * ws / t_sec / 1e6
+    value, t_sec = aggregate_over_ranks(dev_ms / 1000.0, float(px_it * args.steps), pg)
+    value /= 1e6
     launches = int(st1["kernel_launches"] - st0["kernel_launches"])
 
     result = {"metric": "Chambolle Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": ws,
