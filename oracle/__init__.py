@@ -14,7 +14,8 @@ Functions and the passages they follow:
 * ``chambolle``      -- fixed-iteration Chambolle projection for one ROF step (Eq. ROF).
 * ``rof_gap``        -- duality gap of a ROF step (diagnostic).
 * ``decompose``      -- TV flow by implicit Euler (Eq. TVflow, Eq. ROF), phi (Eq. TVtrafo),
-  S(t) (Sec. 2.1), bands (Eq. spectral_bands) and residual (Eq. finite_inverse_trafo).
+  S(t) (Sec. 2.1), bands (Eq. spectral_bands), residual (Eq. finite_inverse_trafo) and
+  filtered images (Eq. filteredTVtrafo substituted into Eq. finite_inverse_trafo).
 """
 from __future__ import annotations
 
@@ -71,6 +72,8 @@ def _lib():
                                         ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]
             h.orc_decompose.restype = ctypes.c_int
+            h.orc_decompose_filtered.argtypes = h.orc_decompose.argtypes + [ctypes.c_int, _dp, _dp, _dp]
+            h.orc_decompose_filtered.restype = ctypes.c_int
             h.orc_max_threads.argtypes = []
             h.orc_max_threads.restype = ctypes.c_int
             _handle = h
@@ -142,11 +145,13 @@ def band_of(t: float, edges) -> int:
 
 
 def decompose(f, dt: float, K: int, n_inner: int, edges, tau: float = 0.125,
-              warm_start: bool = True, trace: bool = False) -> dict:
+              warm_start: bool = True, trace: bool = False, filters=None) -> dict:
     """Spectral TV decomposition of ``f`` (H x W).
 
     Returns a dict with ``bands`` ((n_edges-1, H, W)), ``residual`` ((H, W)), ``S`` ((K-1,))
     and, when ``trace`` is set, ``u`` ((K+1, H, W)) holding u_0..u_K. All float64.
+    ``filters``: optional list of (H_values, h_r) with H_values[k-1] = H(t_k) for k=1..K-1;
+    adds ``filtered`` ((n_filters, H, W)) = sum_k H(t_k) phi_k dt + h_r f_r (Eq. filteredTVtrafo).
     """
     f = _f64(f)
     if f.ndim != 2:
@@ -158,14 +163,21 @@ def decompose(f, dt: float, K: int, n_inner: int, edges, tau: float = 0.125,
     residual = np.zeros((H, W))
     S = np.zeros(max(K - 1, 0))
     ut = np.zeros((K + 1, H, W)) if trace else None
-    rc = _lib().orc_decompose(_ptr(f), H, W, float(dt), int(K), int(n_inner), float(tau),
-                              1 if warm_start else 0, _ptr(e), len(e), _ptr(bands),
-                              _ptr(residual), _ptr(S), _ptr(ut) if trace else None)
+    nf = len(filters) if filters else 0
+    fH = _f64([np.asarray(h, np.float64).reshape(K - 1) for h, _ in filters]) if nf else np.zeros(1)
+    fr = _f64([r for _, r in filters]) if nf else np.zeros(1)
+    filtered = np.zeros((max(nf, 1), H, W))
+    rc = _lib().orc_decompose_filtered(_ptr(f), H, W, float(dt), int(K), int(n_inner), float(tau),
+                                       1 if warm_start else 0, _ptr(e), len(e), _ptr(bands),
+                                       _ptr(residual), _ptr(S), _ptr(ut) if trace else None,
+                                       nf, _ptr(fH), _ptr(fr), _ptr(filtered))
     if rc == -2:
         raise ValueError("oracle: invalid arguments")
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
     out = {"bands": bands, "residual": residual, "S": S}
+    if nf:
+        out["filtered"] = filtered
     if trace:
         out["u"] = ut
     return out

@@ -16,6 +16,8 @@
  *     by a second time difference, its spectrum S(t) = |phi(t)|_L1           (Sec. 2.1)
  *   - band sums b^m = int_{e_m}^{e_{m+1}} phi dt                               (Eq. spectral_bands)
  *   - the residual f_r(T) = u(T) - T u_t(T)                                   (Eq. finite_inverse_trafo)
+ *   - filtered images f_H = int_0^T phi(t) H(t) dt + h_r f_r                  (Eq. filteredTVtrafo
+ *     substituted into Eq. finite_inverse_trafo; h_r weighs the residual)
  *
  * Readings of points the paper leaves open (each one is listed in the design notes):
  *   - forward differences with a zero last row/column (Neumann), divergence = -grad^T;
@@ -189,11 +191,16 @@ int orc_band_of(double t, const double *edges, int n_edges)
  *   residual H*W: f_r = u_{K-1} - t_{K-1} (u_K - u_{K-1}) / dt
  *   S        K-1 values, S[k-1] = sum_ij |phi_k(i,j)|
  *   u_trace  (K+1)*H*W copies of u_0..u_K, or NULL
+ *   filters  n_filters filters: filter_H[q*(K-1) + k-1] = H_q(t_k), filter_res[q] = h_r of
+ *            filter q; filtered (n_filters*H*W) receives
+ *            f_Hq = sum_{k=1}^{K-1} H_q(t_k) phi_k dt + h_r f_r  (Riemann sum, as the bands)
  * Returns 0, -1 on allocation failure, -2 on invalid arguments.
  */
-int orc_decompose(const double *f, int H, int W, double dt, int K, int n_inner, double tau,
-                  int warm_start, const double *edges, int n_edges, double *bands,
-                  double *residual, double *S, double *u_trace)
+int orc_decompose_filtered(const double *f, int H, int W, double dt, int K, int n_inner,
+                           double tau, int warm_start, const double *edges, int n_edges,
+                           double *bands, double *residual, double *S, double *u_trace,
+                           int n_filters, const double *filter_H, const double *filter_res,
+                           double *filtered)
 {
     if (H < 1 || W < 1 || K < 2 || n_inner < 0 || !(dt > 0.0) || n_edges < 2)
         return -2;
@@ -210,6 +217,8 @@ int orc_decompose(const double *f, int H, int W, double dt, int K, int n_inner, 
     }
     memcpy(u_cur, f, N * sizeof(double)); /* u_0 = f  (Eq. TVflow, u(0) = f) */
     memset(bands, 0, (size_t)n_bands * N * sizeof(double));
+    if (n_filters > 0)
+        memset(filtered, 0, (size_t)n_filters * N * sizeof(double));
     if (u_trace)
         memcpy(u_trace, u_cur, N * sizeof(double));
 
@@ -236,6 +245,9 @@ int orc_decompose(const double *f, int H, int W, double dt, int K, int n_inner, 
                 s += fabs(phi);                              /* S(t) = |phi(t)|_L1 */
                 if (m >= 0)
                     bands[(size_t)m * N + n] += phi * dt;    /* Eq. spectral_bands */
+                for (int q = 0; q < n_filters; ++q)          /* Eq. filteredTVtrafo */
+                    filtered[(size_t)q * N + n] +=
+                        filter_H[(size_t)q * (K - 1) + (k - 1)] * phi * dt;
             }
             S[k - 1] = s;
         }
@@ -250,7 +262,19 @@ int orc_decompose(const double *f, int H, int W, double dt, int K, int n_inner, 
         double T = (double)(K - 1) * dt;
         for (size_t n = 0; n < N; ++n)
             residual[n] = u_prev[n] - T * (u_cur[n] - u_prev[n]) / dt;
+        for (int q = 0; q < n_filters; ++q)
+            for (size_t n = 0; n < N; ++n)
+                filtered[(size_t)q * N + n] += filter_res[q] * residual[n];
     }
     free(u_prev); free(u_cur); free(u_next); free(p1); free(p2);
     return rc;
+}
+
+/* The decomposition without filters. */
+int orc_decompose(const double *f, int H, int W, double dt, int K, int n_inner, double tau,
+                  int warm_start, const double *edges, int n_edges, double *bands,
+                  double *residual, double *S, double *u_trace)
+{
+    return orc_decompose_filtered(f, H, W, dt, K, n_inner, tau, warm_start, edges, n_edges,
+                                  bands, residual, S, u_trace, 0, NULL, NULL, NULL);
 }

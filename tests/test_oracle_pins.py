@@ -335,3 +335,47 @@ def test_warm_and_cold_start_agree_when_converged():
         b = oracle.decompose(f, 0.5, 4, n, syn.DYADIC_EDGES, warm_start=False, trace=True)
         diffs.append(np.abs(a["u"] - b["u"]).max())
     assert diffs[1] <= 1e-4 and diffs[1] < 0.5 * diffs[0], diffs
+
+
+# --------------------------------------------------------------------------------------------
+# Spectral filtering (Eq. filteredTVtrafo): f_H = sum_k H(t_k) phi_k dt + h_r f_r
+# --------------------------------------------------------------------------------------------
+def _filt_setup():
+    dt, K = 0.5, 12
+    f = syn.make_image(22, 27, 6, (2, 8), (0.1, 1.0), 0.03, seed=31).astype(np.float64)
+    tk = dt * np.arange(1, K)
+    return f, dt, K, tk
+
+
+def test_all_pass_filter_reconstructs_the_image():
+    f, dt, K, tk = _filt_setup()
+    out = oracle.decompose(f, dt, K, 40, syn.DYADIC_EDGES, filters=[(np.ones(K - 1), 1.0)])
+    assert np.max(np.abs(out["filtered"][0] - f)) <= 1e-12 * np.abs(f).max()
+
+
+def test_band_indicator_filter_equals_the_band_exactly():
+    f, dt, K, tk = _filt_setup()
+    e = syn.DYADIC_EDGES
+    filters = [(((e[m] <= tk) & (tk < e[m + 1])).astype(float), 0.0) for m in range(len(e) - 1)]
+    out = oracle.decompose(f, dt, K, 40, e, filters=filters)
+    assert np.array_equal(out["filtered"], out["bands"])
+
+
+def test_complementary_filters_sum_to_the_image_and_filters_are_linear():
+    f, dt, K, tk = _filt_setup()
+    low = np.exp(-tk / 2.0)            # passes small scales
+    high = 1.0 - low
+    a, b = 0.7, -1.3
+    out = oracle.decompose(f, dt, K, 40, syn.DYADIC_EDGES,
+                           filters=[(low, 0.25), (high, 0.75), (a * low + b * high, a * 0.25 + b * 0.75)])
+    fl, fh, fc = out["filtered"]
+    assert np.max(np.abs(fl + fh - f)) <= 1e-12 * np.abs(f).max()
+    assert np.max(np.abs(fc - (a * fl + b * fh))) <= 1e-12 * np.abs(f).max()
+
+
+def test_filtering_is_one_homogeneous_exactly():
+    f, dt, K, tk = _filt_setup()
+    h = np.cos(tk)
+    a = oracle.decompose(f, dt, K, 40, syn.DYADIC_EDGES, filters=[(h, 0.5)])
+    b = oracle.decompose(2 * f, 2 * dt, K, 40, tuple(2 * x for x in syn.DYADIC_EDGES), filters=[(h, 0.5)])
+    assert np.array_equal(b["filtered"], 2 * a["filtered"])
