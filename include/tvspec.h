@@ -107,6 +107,14 @@ typedef struct {
     double *S;              /* out: K-1 values, S[k-1] = S(t_k) */
     double *u_trace;        /* out, optional (NULL): (K+1)*H*W values of u_0..u_K in float64 */
     int mem_kind;           /* TVSPEC_MEM_HOST or TVSPEC_MEM_DEVICE */
+    /* Spectral filtering (Eq. filteredTVtrafo substituted into Eq. finite_inverse_trafo),
+     * fused into the per-step epilogue: filter q gives
+     *     filtered_q = sum_{k=1}^{K-1} H_q(t_k) phi_k dt + h_q f_r
+     * (H_q = 1, h_q = 1 reconstructs f; H_q = the indicator of a band, h_q = 0, gives that band). */
+    int n_filters;              /* 0 <= n_filters <= 64 */
+    const double *filter_H;     /* host: n_filters*(K-1) finite values, H_q(t_k) at q*(K-1) + k-1 */
+    const double *filter_residual; /* host: n_filters finite weights h_q of the residual */
+    float *filtered;            /* out: n_filters*H*W images (mem_kind memory) */
 } tvspec_request;
 
 typedef struct {

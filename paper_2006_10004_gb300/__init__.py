@@ -51,7 +51,9 @@ class Request(ctypes.Structure):
                 ("dt", ctypes.c_double), ("K", ctypes.c_int), ("n_inner", ctypes.c_int),
                 ("band_edges", ctypes.c_void_p), ("n_edges", ctypes.c_int),
                 ("bands", ctypes.c_void_p), ("residual", ctypes.c_void_p), ("S", ctypes.c_void_p),
-                ("u_trace", ctypes.c_void_p), ("mem_kind", ctypes.c_int)]
+                ("u_trace", ctypes.c_void_p), ("mem_kind", ctypes.c_int),
+                ("n_filters", ctypes.c_int), ("filter_H", ctypes.c_void_p),
+                ("filter_residual", ctypes.c_void_p), ("filtered", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -208,10 +210,23 @@ class Plan:
     def _edges(edges) -> np.ndarray:
         return np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
 
-    def _make_request(self, f, dt, K, n_inner, edges, trace, keep):
+    @staticmethod
+    def _filters(filters, K):
+        """filters: list of (H_values, h_r), H_values[k-1] = H(t_k) for k = 1..K-1."""
+        nf = len(filters) if filters else 0
+        if nf == 0:
+            return 0, None, None
+        fH = np.ascontiguousarray(np.stack([np.asarray(h, np.float64).reshape(max(K - 1, 0))
+                                            for h, _ in filters]))
+        fr = np.ascontiguousarray(np.asarray([float(r) for _, r in filters], np.float64))
+        return nf, fH, fr
+
+    def _make_request(self, f, dt, K, n_inner, edges, trace, keep, filters=None):
         e = self._edges(edges)
         keep.append(e)
         nb = len(e) - 1
+        nf, fH, fr = self._filters(filters, K)
+        keep.extend([fH, fr])
         if _is_torch_cuda(f):
             import torch
 
@@ -225,6 +240,8 @@ class Plan:
                          S=torch.empty((max(K - 1, 0),), dtype=torch.float64, device=dev))
             if trace:
                 out["u"] = torch.empty((K + 1, H, W), dtype=torch.float64, device=dev)
+            if nf:
+                out["filtered"] = torch.empty((nf, H, W), dtype=torch.float32, device=dev)
             ptr = lambda t: t.data_ptr()
             kind = MEM_DEVICE
         else:
@@ -236,19 +253,29 @@ class Plan:
                          S=np.zeros((max(K - 1, 0),), np.float64))
             if trace:
                 out["u"] = np.zeros((K + 1, H, W), np.float64)
+            if nf:
+                out["filtered"] = np.zeros((nf, H, W), np.float32)
             ptr = lambda a: a.ctypes.data
             kind = MEM_HOST
         keep.append(f)
         r = Request(f=ptr(f), H=H, W=W, dt=float(dt), K=int(K), n_inner=int(n_inner),
                     band_edges=e.ctypes.data, n_edges=len(e), bands=ptr(out["bands"]),
                     residual=ptr(out["residual"]), S=ptr(out["S"]) if K > 1 else ptr(out["residual"]),
-                    u_trace=ptr(out["u"]) if trace else None, mem_kind=kind)
+                    u_trace=ptr(out["u"]) if trace else None, mem_kind=kind, n_filters=nf,
+                    filter_H=fH.ctypes.data if nf else None,
+                    filter_residual=fr.ctypes.data if nf else None,
+                    filtered=ptr(out["filtered"]) if nf else None)
         return r, out, kind
 
-    def decompose(self, f, dt: float, K: int, n_inner: int, edges, trace: bool = False, stream=None):
-        """Decompose one image; returns a Result (numpy for host input, torch for CUDA input)."""
+    def decompose(self, f, dt: float, K: int, n_inner: int, edges, trace: bool = False, stream=None,
+                  filters=None):
+        """Decompose one image; returns a Result (numpy for host input, torch for CUDA input).
+
+        ``filters``: optional list of (H_values, h_r) spectral filters (Eq. filteredTVtrafo);
+        the Result then holds ``filtered`` ((n_filters, H, W)).
+        """
         keep = []
-        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep)
+        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep, filters)
         st = _stream_ptr(stream) if kind == MEM_DEVICE else None
         _check(self._lib.tvspec_decompose_ex(self._h, ctypes.byref(r), st), "tvspec_decompose_ex")
         return out
@@ -262,11 +289,13 @@ class Plan:
                "tvspec_decompose")
 
     def decompose_batch(self, jobs, trace: bool = False, stream=None):
-        """jobs: iterable of (f, dt, K, n_inner, edges). Returns a list of Results."""
+        """jobs: iterable of (f, dt, K, n_inner, edges[, filters]). Returns a list of Results."""
         keep = []
         reqs, outs, kinds = [], [], set()
-        for (f, dt, K, n_inner, edges) in jobs:
-            r, o, k = self._make_request(f, dt, K, n_inner, edges, trace, keep)
+        for job in jobs:
+            f, dt, K, n_inner, edges = job[:5]
+            r, o, k = self._make_request(f, dt, K, n_inner, edges, trace, keep,
+                                         job[5] if len(job) > 5 else None)
             reqs.append(r)
             outs.append(o)
             kinds.add(k)
@@ -278,10 +307,10 @@ class Plan:
         return outs
 
     # ---- serving -------------------------------------------------------------------------------
-    def submit(self, f, dt, K, n_inner, edges, trace: bool = False):
+    def submit(self, f, dt, K, n_inner, edges, trace: bool = False, filters=None):
         """Queue one host-memory request; returns (ticket, Result). Keep the Result alive."""
         keep = []
-        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep)
+        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep, filters)
         if kind != MEM_HOST:
             raise TypeError("serving takes host (numpy) images")
         t = ctypes.c_uint64()
@@ -370,7 +399,7 @@ def decompose_noalloc(f, dt: float, K: int, n_inner: int, edges, stream=None) ->
     return out
 
 
-def validate(f_shape, dt, K, n_inner, edges, f=None, mem_kind=MEM_HOST) -> int:
+def validate(f_shape, dt, K, n_inner, edges, f=None, mem_kind=MEM_HOST, filters=None) -> int:
     """Host-only argument check through tvspec_validate (no GPU needed); returns the status."""
     L = load()
     H, W = f_shape
@@ -378,9 +407,15 @@ def validate(f_shape, dt, K, n_inner, edges, f=None, mem_kind=MEM_HOST) -> int:
     fa = np.zeros((H, W), np.float32) if f is None else np.ascontiguousarray(np.asarray(f, np.float32))
     dummy = np.zeros(max(1, (len(e) - 1) * H * W), np.float32)
     S = np.zeros(max(1, K), np.float64)
+    nf = len(filters) if filters else 0
+    fH = np.ascontiguousarray(np.concatenate([np.asarray(h, np.float64).ravel() for h, _ in filters])) if nf else None
+    fr = np.ascontiguousarray(np.asarray([float(r) for _, r in filters], np.float64)) if nf else None
+    fout = np.zeros(max(1, nf * H * W), np.float32)
     r = Request(f=fa.ctypes.data, H=H, W=W, dt=float(dt), K=int(K), n_inner=int(n_inner),
                 band_edges=e.ctypes.data, n_edges=len(e), bands=dummy.ctypes.data, residual=dummy.ctypes.data,
-                S=S.ctypes.data, u_trace=None, mem_kind=mem_kind)
+                S=S.ctypes.data, u_trace=None, mem_kind=mem_kind, n_filters=nf,
+                filter_H=fH.ctypes.data if nf else None, filter_residual=fr.ctypes.data if nf else None,
+                filtered=fout.ctypes.data if nf else None)
     return int(L.tvspec_validate(ctypes.byref(r)))
 
 

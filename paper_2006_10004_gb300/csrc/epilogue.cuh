@@ -20,7 +20,8 @@ __device__ __forceinline__ double div_at(int i, int j, int H, int W, float p1_ij
 //   u_{k+1} = u_k - dt div p                                    (primal recovery, Eq. ROF)
 //   phi_k   = t_k (u_{k+1} - 2 u_k + u_{k-1}) / dt^2, k >= 1       (Eq. TVtrafo)
 //   band accumulation, band flush and residual at the last step (Eq. spectral_bands,
-//   Eq. finite_inverse_trafo); u_{k+1} replaces u_{k-1} in the ping-pong buffer.
+//   Eq. finite_inverse_trafo), spectral filters (Eq. filteredTVtrafo); u_{k+1} replaces
+//   u_{k-1} in the ping-pong buffer.
 // Returns |phi_k| (0 at k = 0) and g/dt of the next step in *gl_next.
 __device__ __forceinline__ double epilogue_pixel(const ImgDesc &d, int k, size_t n, double divp,
                                                  float *gl_next) {
@@ -48,12 +49,21 @@ __device__ __forceinline__ double epilogue_pixel(const ImgDesc &d, int k, size_t
             else d.bands[(size_t)mp * N + n] = (float)old;  // band mp is complete
         }
         if (m >= 0) acc = __dadd_rn(acc, __dmul_rn(phi, d.dt));
-        if (k == d.K - 1) {
+        const bool last = k == d.K - 1;
+        const double resid =
+            last ? __dsub_rn(uc, __dmul_rn(__dmul_rn(tk, __dsub_rn(un, uc)), d.inv_dt)) : 0.0;
+        if (last) {
             if (m >= 0) d.bands[(size_t)m * N + n] = (float)acc;
-            d.residual[n] =
-                (float)__dsub_rn(uc, __dmul_rn(__dmul_rn(tk, __dsub_rn(un, uc)), d.inv_dt));
+            d.residual[n] = (float)resid;
         } else {
             d.acc[n] = acc;
+        }
+        // spectral filters: sum_k H_q(t_k) phi_k dt + h_q f_r   (Eq. filteredTVtrafo)
+        for (int q = 0; q < d.n_filters; ++q) {
+            double fa = (k >= 2) ? d.facc[(size_t)q * N + n] : 0.0;
+            fa = __dadd_rn(fa, __dmul_rn(__dmul_rn(d.filt_H[(size_t)q * (d.K - 1) + (k - 1)], phi), d.dt));
+            if (last) d.filtered[(size_t)q * N + n] = (float)__dadd_rn(fa, __dmul_rn(d.filt_res[q], resid));
+            else d.facc[(size_t)q * N + n] = fa;
         }
     }
     uoth[n] = un;

@@ -57,6 +57,16 @@ tvspec_status make_job(const tvspec_request &req, Job *out) {
         if (!std::isfinite(e[m]) && m != req.n_edges - 1)
             return fail(TVSPEC_EINVAL, "only the last band edge may be infinite");
     }
+    if (req.n_filters < 0 || req.n_filters > 64) return fail(TVSPEC_EINVAL, "n_filters must be in [0, 64]");
+    if (req.n_filters > 0) {
+        if (!req.filter_H || !req.filter_residual || !req.filtered)
+            return fail(TVSPEC_EINVAL, "filter_H, filter_residual and filtered must be non-NULL");
+        for (size_t q = 0; q < (size_t)req.n_filters * (req.K - 1); ++q)
+            if (!std::isfinite(req.filter_H[q])) return fail(TVSPEC_EINVAL, "filter value is not finite");
+        for (int q = 0; q < req.n_filters; ++q)
+            if (!std::isfinite(req.filter_residual[q]))
+                return fail(TVSPEC_EINVAL, "filter residual weight is not finite");
+    }
     if (req.mem_kind == TVSPEC_MEM_HOST) {
         const size_t N = (size_t)req.H * (size_t)req.W;
         for (size_t n = 0; n < N; ++n)
@@ -74,6 +84,15 @@ tvspec_status make_job(const tvspec_request &req, Job *out) {
             }
     }
     out->r.band_edges = out->edges.data();
+    if (req.n_filters > 0) {
+        out->filt_H.assign(req.filter_H, req.filter_H + (size_t)req.n_filters * (req.K - 1));
+        out->filt_res.assign(req.filter_residual, req.filter_residual + req.n_filters);
+        out->r.filter_H = out->filt_H.data();
+        out->r.filter_residual = out->filt_res.data();
+    } else {
+        out->r.filter_H = nullptr;
+        out->r.filter_residual = nullptr;
+    }
     return TVSPEC_OK;
 }
 
@@ -83,11 +102,12 @@ tvspec_status make_job(const tvspec_request &req, Job *out) {
 // The part from p1 to the status word is cleared at the start of every decomposition.
 // ---------------------------------------------------------------------------------------------
 struct SlotLayout {
-    size_t band, f, p1, p2, q1, q2, gl, acc, bands, partials, ctr, ua, ub, res, S, tr, zero_begin,
-        zero_end, total;
+    size_t band, fH, fres, f, p1, p2, q1, q2, gl, acc, facc, filt, bands, partials, ctr, ua, ub,
+        res, S, tr, zero_begin, zero_end, total;
 };
 
-static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naive, bool trace) {
+static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naive, bool trace,
+                             int nf = 0) {
     SlotLayout L{};
     const size_t N = (size_t)H * W;
     const int pitch = pitch_for(W);
@@ -99,6 +119,8 @@ static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naiv
         return o;
     };
     L.band = take(K);
+    L.fH = take((size_t)nf * (K - 1) * 8);
+    L.fres = take((size_t)nf * 8);
     L.f = take(N * 4);
     L.zero_begin = off;
     L.p1 = take(pb);
@@ -111,6 +133,8 @@ static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naiv
     L.partials = take((size_t)ep_blocks_for(H, W) * 8);
     L.ctr = take(16);
     L.zero_end = off;
+    L.facc = take((size_t)nf * N * 8);  // written at k = 1 before any read
+    L.filt = take((size_t)nf * N * 4);
     L.ua = take(N * 8);
     L.ub = take(N * 8);
     L.res = take(N * 4);
@@ -121,7 +145,8 @@ static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naiv
 }
 
 size_t slot_bytes_for(const Job &j, int storage, bool naive) {
-    return layout_for(j.r.H, j.r.W, j.r.K, j.r.n_edges - 1, storage, naive, j.r.u_trace != nullptr)
+    return layout_for(j.r.H, j.r.W, j.r.K, j.r.n_edges - 1, storage, naive, j.r.u_trace != nullptr,
+                      j.r.n_filters)
         .total;
 }
 
@@ -130,7 +155,7 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
     const tvspec_request &r = j.r;
     const bool trace = r.u_trace != nullptr;
     const int nb = r.n_edges - 1;
-    const SlotLayout L = layout_for(r.H, r.W, r.K, nb, storage, naive, trace);
+    const SlotLayout L = layout_for(r.H, r.W, r.K, nb, storage, naive, trace, r.n_filters);
     char *base = nullptr;
     cudaError_t e = async_alloc ? cudaMallocAsync((void **)&base, L.total, st)
                                 : cudaMalloc((void **)&base, L.total);
@@ -171,9 +196,18 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
     x.residual = (float *)(base + L.res);
     x.S = (double *)(base + L.S);
     x.utrace = trace ? (double *)(base + L.tr) : nullptr;
+    x.n_filters = r.n_filters;
+    x.filt_H = (double *)(base + L.fH);
+    x.filt_res = (double *)(base + L.fres);
+    x.facc = (double *)(base + L.facc);
+    x.filtered = (float *)(base + L.filt);
     x.ep_blocks = ep_blocks_for(r.H, r.W);
     x.p_bytes = (size_t)r.H * x.pitch * storage_bytes(storage);
     e = cudaMemcpyAsync(x.band_of_k, j.band_of_k.data(), r.K, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && r.n_filters > 0)
+        e = cudaMemcpyAsync(x.filt_H, j.filt_H.data(), j.filt_H.size() * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && r.n_filters > 0)
+        e = cudaMemcpyAsync(x.filt_res, j.filt_res.data(), j.filt_res.size() * 8, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
         if (async_alloc) cudaFreeAsync(base, st); else cudaFree(base);
         return fail_cuda(e, "band table upload");
@@ -209,6 +243,11 @@ ImgDesc slot_desc(const Slot &s, int s0) {
     d.counter = s.counter;
     d.status = s.status;
     d.band_of_k = s.band_of_k;
+    d.n_filters = s.n_filters;
+    d.filt_H = s.filt_H;
+    d.filt_res = s.filt_res;
+    d.facc = s.facc;
+    d.filtered = s.filtered;
     d.H = s.H;
     d.W = s.W;
     d.pitch = s.pitch;
@@ -534,6 +573,9 @@ static std::string job_key(const tvspec_config &c, const std::vector<Job> &jobs)
         k << ';' << j.r.H << 'x' << j.r.W << ',' << j.r.K << ',' << j.r.n_inner << ',' << j.r.dt
           << ',' << (j.r.u_trace ? 1 : 0);
         for (double e : j.edges) k << ',' << e;
+        k << ",f" << j.r.n_filters;
+        for (double v : j.filt_H) k << ',' << v;
+        for (double v : j.filt_res) k << ',' << v;
     }
     return k.str();
 }
@@ -703,6 +745,8 @@ static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStr
         TV_CK(cudaMemcpyAsync(r.S, sl.S, (size_t)(r.K - 1) * 8, out_kind, st));
         if (r.u_trace)
             TV_CK(cudaMemcpyAsync(r.u_trace, sl.utrace, (size_t)(r.K + 1) * N * 8, out_kind, st));
+        if (r.n_filters > 0)
+            TV_CK(cudaMemcpyAsync(r.filtered, sl.filtered, (size_t)r.n_filters * N * 4, out_kind, st));
         TV_CK(cudaMemcpyAsync(E->h_status + i, sl.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     }
     if (user_st) {

@@ -34,6 +34,7 @@ struct Job {
     tvspec_request r;
     std::vector<double> edges;
     std::vector<signed char> band_of_k;  // K entries (entry 0 unused)
+    std::vector<double> filt_H, filt_res; // n_filters x (K-1), n_filters
 };
 tvspec_status make_job(const tvspec_request &req, Job *out);
 
@@ -53,6 +54,9 @@ struct Slot {
     double *S = nullptr, *utrace = nullptr, *partials = nullptr;
     unsigned *counter = nullptr, *status = nullptr;
     signed char *band_of_k = nullptr;
+    int n_filters = 0;
+    double *filt_H = nullptr, *filt_res = nullptr, *facc = nullptr;
+    float *filtered = nullptr;
     int ep_blocks = 0;
     size_t p_bytes = 0;  // bytes of one pitched p array (one component, one copy)
 };

@@ -36,6 +36,11 @@ struct ImgDesc {
                             // hold the persistent kernel's grid barrier (arrivals, generation)
     unsigned *status;       // device status bits (counter + 1)
     const signed char *band_of_k;  // K entries: band of t_k (host-decided in float64), -1 none
+    int n_filters;          // spectral filters fused into the epilogue
+    const double *filt_H;   // n_filters x (K-1): H_q(t_k) at q*(K-1) + k-1
+    const double *filt_res; // n_filters residual weights
+    double *facc;           // n_filters x H x W running filter sums (compact)
+    float *filtered;        // n_filters x H x W output (compact), device
     int H, W, pitch;
     int K, n_inner;
     int s0;                 // global step at which this image's step 0 runs

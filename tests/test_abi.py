@@ -79,6 +79,18 @@ def test_validate_rejects_non_finite_host_image():
     assert tv.validate((4, 4), 0.5, 4, 10, (0, INF), f=f) == tv.EINVAL
 
 
+def test_validate_filters():
+    K = 6
+    ok = [(np.ones(K - 1), 1.0), (np.linspace(0, 1, K - 1), 0.0)]
+    assert tv.validate((8, 8), 0.5, K, 10, (0, INF), filters=ok) == tv.OK
+    assert tv.validate((8, 8), 0.5, K, 10, (0, INF), filters=[(np.ones(K - 1), 1.0)] * 64) == tv.OK
+    assert tv.validate((8, 8), 0.5, K, 10, (0, INF), filters=[(np.ones(K - 1), 1.0)] * 65) == tv.EINVAL
+    h = np.ones(K - 1)
+    h[2] = np.nan
+    assert tv.validate((8, 8), 0.5, K, 10, (0, INF), filters=[(h, 1.0)]) == tv.EINVAL
+    assert tv.validate((8, 8), 0.5, K, 10, (0, INF), filters=[(np.ones(K - 1), INF)]) == tv.EINVAL
+
+
 def test_null_arguments_are_rejected_without_a_gpu():
     lib = tv.load()
     assert lib.tvspec_validate(None) == tv.EINVAL
