@@ -349,6 +349,7 @@ def run_gb300(args):
         ms = e0.elapsed_time(e1) / 3
         result["m1024"] = {"workload": syn.m1024.__doc__.strip().splitlines()[0], "decomps_per_s": 1000.0 / ms,
                            "ms_per_decomp": ms, "Mpx_iter_per_s": m.px_iters / ms / 1e3}
+        result["filter_bank_config1"] = measure_filters(tv, torch, plan, job, f_dev, stream, flush)
         result["batched_config2"] = measure_batched(tv, torch, local, 2, 1)
         result["training_crops"] = measure_crops(tv, torch, local)
         sv = measure_serving(tv, local, [float(args.serve_rate)], args.serve_requests)[0]
@@ -360,6 +361,45 @@ def run_gb300(args):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def filter_bank(dt: float, K: int, n: int = 6):
+    """n spectral filters H(t_k): all-pass, ideal low / high / band-pass in t, and smooth ones."""
+    t = dt * np.arange(1, K)
+    bank = [(np.ones(K - 1), 1.0), ((t < 2.0) * 1.0, 0.0), ((t >= 2.0) * 1.0, 1.0),
+            (((t >= 1.0) & (t < 4.0)) * 1.0, 0.0)]
+    s = 2.0
+    while len(bank) < n:
+        bank.append((np.exp(-t / s), 0.5))
+        s *= 2.0
+    return bank[:n]
+
+
+def measure_filters(tv, torch, plan, job, f_dev, stream, flush, n_filters: int = 6, reps: int = 3):
+    """Spectral filtering fused into the epilogue (Eq. filteredTVtrafo): device time of the
+    decomposition with a bank of filters against the same decomposition without, L2 flushed."""
+    bank = filter_bank(job.dt, job.K, n_filters)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        evs = []
+        for i in range(reps):
+            flush.fill_(i & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in evs) / reps
+
+    plain = timed(lambda: plan.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream))
+    filt = timed(lambda: plan.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream,
+                                        filters=bank))
+    return {"filters": n_filters, "ms_with_filters": filt, "ms_without": plain,
+            "overhead_frac": filt / plain - 1.0,
+            "Mpx_iter_per_s_with_filters": job.px_iters / filt / 1e3}
 
 
 def measure_batched(tv, torch, local, steps: int, warmup: int, with_clocks=None):

@@ -16,6 +16,9 @@ Functions and the passages they follow:
 * ``decompose``      -- TV flow by implicit Euler (Eq. TVflow, Eq. ROF), phi (Eq. TVtrafo),
   S(t) (Sec. 2.1), bands (Eq. spectral_bands), residual (Eq. finite_inverse_trafo) and
   filtered images (Eq. filteredTVtrafo substituted into Eq. finite_inverse_trafo).
+* ``crop`` / ``standardize`` / ``training_set`` -- the ground-truth generation of Sec. 4.1:
+  fixed-size crops (some from twice-as-large windows downsampled by 2), standardisation to
+  zero mean and unit standard deviation, then ``decompose`` of every crop.
 """
 from __future__ import annotations
 
@@ -74,6 +77,11 @@ def _lib():
             h.orc_decompose.restype = ctypes.c_int
             h.orc_decompose_filtered.argtypes = h.orc_decompose.argtypes + [ctypes.c_int, _dp, _dp, _dp]
             h.orc_decompose_filtered.restype = ctypes.c_int
+            h.orc_crop.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, _dp]
+            h.orc_crop.restype = ctypes.c_int
+            h.orc_standardize.argtypes = [_dp, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, _dp, _dp]
+            h.orc_standardize.restype = ctypes.c_int
             h.orc_max_threads.argtypes = []
             h.orc_max_threads.restype = ctypes.c_int
             _handle = h
@@ -181,3 +189,51 @@ def decompose(f, dt: float, K: int, n_inner: int, edges, tau: float = 0.125,
     if trace:
         out["u"] = ut
     return out
+
+
+def crop(src, y: int, x: int, size: int, scale: int = 1) -> np.ndarray:
+    """The ``scale``-fold block average of the (scale*size)^2 window of ``src`` at (y, x),
+    rounded to float32 values (returned as float64)."""
+    src = _f64(src)
+    sH, sW = src.shape
+    out = np.zeros((size, size))
+    rc = _lib().orc_crop(_ptr(src), sH, sW, int(y), int(x), int(size), int(scale), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle: crop window outside the source image")
+    return out
+
+
+def standardize(x, mode: int, mean_std=None):
+    """Standardise images x ((n, H, W)): mode 0 none, 1 over all of x, 2 per image, 3 by the
+    given (mean, std). Returns (out, mean_std) with mean_std of length 2 (modes 1, 3) or 2n."""
+    x = _f64(x)
+    n = x.shape[0]
+    npx = int(np.prod(x.shape[1:]))
+    ms = np.zeros(max(2, 2 * n))
+    if mode == 3:
+        ms[0], ms[1] = float(mean_std[0]), float(mean_std[1])
+    out = np.zeros_like(x)
+    rc = _lib().orc_standardize(_ptr(x), n, npx, int(mode), _ptr(ms), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle: bad standardisation mode")
+    return out, (ms[:2 * n] if mode == 2 else ms[:2])
+
+
+def training_set(sources, crops, size: int, standardize_mode: int, dt: float, K: int, n_inner: int,
+                 edges, mean_std=None, tau: float = 0.125, warm_start: bool = True) -> dict:
+    """Ground-truth generation (Sec. 4.1). ``crops``: list of (src_index, y, x, scale).
+
+    Returns ``crops`` ((n, size, size), standardised), ``mean_std``, ``bands``
+    ((n, n_bands, size, size)), ``residual`` ((n, size, size)) and ``S`` ((n, K-1)).
+    """
+    raw = np.stack([crop(sources[c[0]], c[1], c[2], size, c[3]) for c in crops]) if crops else \
+        np.zeros((0, size, size))
+    x, ms = standardize(raw, standardize_mode, mean_std)
+    nb = len(edges) - 1
+    bands = np.zeros((len(crops), nb, size, size))
+    residual = np.zeros((len(crops), size, size))
+    S = np.zeros((len(crops), max(K - 1, 0)))
+    for i in range(len(crops)):
+        r = decompose(x[i], dt, K, n_inner, edges, tau=tau, warm_start=warm_start)
+        bands[i], residual[i], S[i] = r["bands"], r["residual"], r["S"]
+    return {"crops": x, "mean_std": ms, "bands": bands, "residual": residual, "S": S}

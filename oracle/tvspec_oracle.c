@@ -278,3 +278,82 @@ int orc_decompose(const double *f, int H, int W, double dt, int K, int n_inner, 
     return orc_decompose_filtered(f, H, W, dt, K, n_inner, tau, warm_start, edges, n_edges,
                                   bands, residual, S, u_trace, 0, NULL, NULL, NULL);
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Training-sample preparation (Sec. 4.1): greyscale crops of a fixed size, some of them taken
+ * from a window twice as large and downsampled by 2, and the standardisation of the data set
+ * to zero mean and unit standard deviation before the ground-truth bands are computed.
+ * Readings: downsampling by s averages each s x s block (area average), the sum taken in
+ * row-major order within the block; the standard deviation is the population one (divisor N);
+ * a zero standard deviation is replaced by 1; each result is rounded to float32, the type the
+ * decomposition reads.
+ * -------------------------------------------------------------------------------------------*/
+
+/* out (size x size) = the s-fold block average of the (s*size) x (s*size) window of src
+ * (sH x sW, row-major) whose top-left pixel is (y, x). Returns -2 if the window leaves src. */
+int orc_crop(const double *src, int sH, int sW, int y, int x, int size, int s, double *out)
+{
+    if (size < 1 || s < 1 || y < 0 || x < 0 || (long)y + (long)s * size > sH ||
+        (long)x + (long)s * size > sW)
+        return -2;
+    for (int i = 0; i < size; ++i) {
+        for (int j = 0; j < size; ++j) {
+            double sum = 0.0;
+            for (int a = 0; a < s; ++a)
+                for (int b = 0; b < s; ++b)
+                    sum += src[(size_t)(y + s * i + a) * sW + (x + s * j + b)];
+            out[(size_t)i * size + j] = (double)(float)(sum / (double)(s * s));
+        }
+    }
+    return 0;
+}
+
+/* Mean and population standard deviation of x[0..n), two passes, sequential sums. */
+static void orc_mean_std(const double *x, size_t n, double *mean, double *sd)
+{
+    double s = 0.0;
+    for (size_t i = 0; i < n; ++i) s += x[i];
+    const double m = s / (double)n;
+    double q = 0.0;
+    for (size_t i = 0; i < n; ++i) q += (x[i] - m) * (x[i] - m);
+    *mean = m;
+    *sd = sqrt(q / (double)n);
+}
+
+/* Standardise n_img images of npx pixels each (x, contiguous) into out.
+ *   mode 0: out = x;
+ *   mode 1: one mean / standard deviation over all n_img * npx values (the data set);
+ *           mean_std[0..1] receives them;
+ *   mode 2: each image by its own; mean_std[2i..2i+1] receives image i's;
+ *   mode 3: by the given mean_std[0], mean_std[1].
+ * out = (float)((x - mean) / sd), sd == 0 replaced by 1. Returns -2 on a bad mode. */
+int orc_standardize(const double *x, int n_img, size_t npx, int mode, double *mean_std, double *out)
+{
+    if (n_img < 0 || mode < 0 || mode > 3) return -2;
+    const size_t total = (size_t)n_img * npx;
+    if (mode == 0) {
+        for (size_t i = 0; i < total; ++i) out[i] = x[i];
+        return 0;
+    }
+    for (int c = 0; c < n_img; ++c) {
+        double m, sd;
+        if (mode == 1) {
+            if (c == 0) orc_mean_std(x, total, &mean_std[0], &mean_std[1]);
+            m = mean_std[0];
+            sd = mean_std[1];
+        } else if (mode == 2) {
+            orc_mean_std(x + (size_t)c * npx, npx, &mean_std[2 * c], &mean_std[2 * c + 1]);
+            m = mean_std[2 * c];
+            sd = mean_std[2 * c + 1];
+        } else {
+            m = mean_std[0];
+            sd = mean_std[1];
+        }
+        if (sd == 0.0) sd = 1.0;
+        for (size_t i = 0; i < npx; ++i) {
+            const size_t k = (size_t)c * npx + i;
+            out[k] = (double)(float)((x[k] - m) / sd);
+        }
+    }
+    return 0;
+}
