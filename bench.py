@@ -214,6 +214,8 @@ def run_gb300(args):
         return run_batched(args, tv, torch, local, ws)
     if args.workload == "config4":
         return run_serving(args, tv, torch, local, ws)
+    if args.workload == "training":
+        return run_training(args, tv, torch, local, ws)
     wl = _workload(args.workload)
     plan = tv.Plan(local, **({"kernel": tv.KERNEL_TILED, "tile": args.tile} if args.tile >= 0 else {}))
     dev = torch.device("cuda", local)
@@ -454,30 +456,75 @@ def measure_batched(tv, torch, local, steps: int, warmup: int, with_clocks=None)
     return out
 
 
+def training_workload(n: int = 3000, size: int = 64, n_sources: int = 16, seed: int = 9000):
+    """The paper's ground-truth generation (Sec. 4.1): n crops of size^2 from synthetic
+    512^2 greyscale sources, one third of them from (2 size)^2 windows downsampled by 2;
+    crop positions drawn here (seeded) and passed in."""
+    srcs = [syn.make_image(512, 512, 40, (2.0, 60.0), (0.05, 1.0), 0.02, seed + i) for i in range(n_sources)]
+    rng = np.random.default_rng(seed)
+    crops = []
+    for c in range(n):
+        s = 2 if c % 3 == 2 else 1
+        i = int(rng.integers(0, n_sources))
+        crops.append((i, int(rng.integers(0, 512 - s * size + 1)), int(rng.integers(0, 512 - s * size + 1)), s))
+    return srcs, crops
+
+
 def measure_crops(tv, torch, local, n: int = 3000):
-    """The paper's ground-truth generation use (Sec. 4.1): many 64x64 greyscale crops, K = 50
-    steps of dt = 0.5, 300 iterations, 6 dyadic bands, as one batch. Device time of the
-    resident path (one CTA per image, one launch) against the per-step path."""
+    """Training-data generation: crops + standardisation over the set + decompositions
+    (K = 50 steps of dt = .5, 300 iterations, 6 dyadic bands) of n 64x64 crops through
+    tvspec_training_set (device memory), against the same standardised crops decomposed as a
+    batch on the per-step path and on the resident path."""
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    crops = [torch.from_numpy(syn.make_image(64, 64, 6, (3.0, 16.0), (0.1, 1.0), 0.01, 9000 + j)).to(dev)
-             for j in range(n)]
-    jobs = [(c, 0.5, 50, 300, syn.DYADIC_EDGES) for c in crops]
-    out = {"workload": f"{n} crops 64x64, K=50, dt=.5, 300 iterations, 6 dyadic bands"}
-    for name, res in (("resident", 1), ("per_step", 0)):
+    srcs, crops = training_workload(n)
+    srcs_d = [torch.from_numpy(x).to(dev) for x in srcs]
+    out = {"workload": f"{n} crops 64x64 (1/3 from 128x128 downsampled by 2) of 16 sources 512x512, "
+                       "standardised over the set, K=50, dt=.5, 300 iterations, 6 dyadic bands"}
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with tv.Plan(local) as p:
+        run = lambda: p.training_set(srcs_d, crops, 64, 1, 0.5, 50, 300, syn.DYADIC_EDGES, want_stats=False,
+                                     stream=stream)
+        ms = timed(run)
+        x = run()["crops"]
+        torch.cuda.synchronize()
+        out["training_set"] = {"images_per_s": n / ms * 1e3, "ms": ms,
+                               "Mpx_iter_per_s": n * 64 * 64 * 50 * 300 / ms / 1e3}
+    jobs = [(x[i], 0.5, 50, 300, syn.DYADIC_EDGES) for i in range(n)]
+    for name, res in (("resident_batch", 1), ("per_step_batch", 0)):
         with tv.Plan(local, resident=res) as p:
-            p.decompose_batch(jobs, stream=stream)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            p.decompose_batch(jobs, stream=stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
+            ms = timed(lambda: p.decompose_batch(jobs, stream=stream), reps=1)
             out[name] = {"images_per_s": n / ms * 1e3, "ms": ms,
                          "Mpx_iter_per_s": n * 64 * 64 * 50 * 300 / ms / 1e3}
-    out["resident_over_per_step"] = out["resident"]["images_per_s"] / out["per_step"]["images_per_s"]
+    out["training_set_over_per_step"] = out["training_set"]["images_per_s"] / out["per_step_batch"]["images_per_s"]
     return out
+
+
+def run_training(args, tv, torch, local, ws):
+    dev = torch.device("cuda", local)
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
+    with ClockSampler(local) as clk:
+        m = measure_crops(tv, torch, local, args.crops)
+    t = m["training_set"]
+    result = {"metric": "Chambolle Mpx*iter/s", "value": t["Mpx_iter_per_s"], "unit": "Mpx*iter/s",
+              "n_gpus": ws, "steps": 2, "warmup": 1, "ms_per_step": t["ms"], "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": m["workload"], "images": args.crops,
+                         "l2": "inputs and workspace (~0.5 GB) larger than L2"},
+              "clocks": clk.summary(), "training": m}
+    print(json.dumps(result))
+    return 0
 
 
 def run_batched(args, tv, torch, local, ws):
@@ -610,7 +657,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="config1", choices=["config1", "m1024", "config2", "config3", "config4"])
+    ap.add_argument("--crops", type=int, default=3000, help="crops of the training workload")
+    ap.add_argument("--workload", default="config1",
+                    choices=["config1", "m1024", "config2", "config3", "config4", "training"])
     ap.add_argument("--rates", default="20,50,100,200", help="config4: Poisson arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=200, help="config4: requests per rate")
     ap.add_argument("--no-e2e", action="store_true")

@@ -162,6 +162,58 @@ tvspec_status tvspec_decompose_ex(tvspec_plan *plan, const tvspec_request *req, 
 tvspec_status tvspec_decompose_batch(tvspec_plan *plan, int n, const tvspec_request *reqs,
                                      void *stream);
 
+/* Ground-truth generation for training (Sec. 4.1): greyscale crops of size x size pixels, some
+ * taken from (scale*size)^2 windows and downsampled by averaging scale x scale blocks (the
+ * paper's 128^2 crops downsampled by 2), standardised to zero mean and unit standard
+ * deviation, then decomposed with one schedule (dt, K, n_inner, band edges) for all crops.
+ *
+ * A crop is (src, y, x, scale): the window of source image `src` with top-left pixel (y, x);
+ * the block average sums a block in row-major order in float64 and rounds the mean to float32.
+ * Random crop positions are drawn by the caller and passed in. */
+typedef struct tvspec_crop {
+    int src;    /* index into sources[] */
+    int y, x;   /* top-left pixel of the window; the window must lie inside the source */
+    int scale;  /* 1..16: window side = scale * size */
+} tvspec_crop;
+
+typedef struct tvspec_training_request {
+    int n_sources;                  /* >= 1 */
+    const float *const *sources;    /* host array of n_sources pointers to row-major images
+                                       (mem_kind memory) */
+    const int *source_H;            /* host, n_sources heights */
+    const int *source_W;            /* host, n_sources widths */
+    int n_crops;                    /* >= 1 */
+    const tvspec_crop *crops;       /* host, n_crops */
+    int size;                       /* crop side, 1..4096 */
+    int standardize;                /* 0 none; 1 one mean / population standard deviation over
+                                       all crops of this call (the data set); 2 each crop by its
+                                       own; 3 by mean_std[0..1]. A zero deviation divides by 1.
+                                       out = (float)((x - mean) / sd) in float64 */
+    double mean_std[2];             /* in, for standardize == 3 */
+    double dt;                      /* > 0 */
+    int K;                          /* ROF steps, 2..100000 */
+    int n_inner;                    /* dual iterations per step, >= 0 */
+    const double *band_edges;       /* host, n_edges increasing t-edges (last may be +inf) */
+    int n_edges;                    /* 2..65 */
+    float *crops_out;               /* out, optional: n_crops*size*size standardised crops */
+    float *bands;                   /* out: n_crops*(n_edges-1)*size*size, crop-major */
+    float *residual;                /* out: n_crops*size*size */
+    double *S;                      /* out: n_crops*(K-1) */
+    double *stats;                  /* out, optional (host): 2 values (standardize 1, 3) or
+                                       2*n_crops (standardize 2): mean, deviation pairs */
+    int mem_kind;                   /* sources and the outputs above (stats: always host) */
+} tvspec_training_request;
+
+/* Runs the whole generation for one request: crop + downsample and standardisation kernels,
+ * the decompositions of all crops as one batch (the resident one-CTA-per-image kernel for
+ * small crops; results bit-identical to tvspec_decompose of each standardised crop), and one
+ * gather of the outputs into the caller's crop-major arrays. Synchronous for TVSPEC_MEM_HOST
+ * (and whenever stats is requested); otherwise enqueued on `stream` like tvspec_decompose.
+ * Errors: EINVAL (bad request, window outside its source, non-finite mean_std), ENOMEM, ECUDA
+ * (including a non-finite value in the flow, detected for TVSPEC_MEM_HOST). */
+tvspec_status tvspec_training_set(tvspec_plan *plan, const tvspec_training_request *req,
+                                  void *stream);
+
 /* Serving (continuous batching). submit copies the request descriptor (not the buffers, which
  * must stay valid until poll returns OK) and returns a ticket at once. A scheduler thread
  * admits requests while their device memory fits mem_budget_bytes, runs one ROF step of every

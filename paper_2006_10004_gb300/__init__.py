@@ -56,6 +56,20 @@ class Request(ctypes.Structure):
                 ("filter_residual", ctypes.c_void_p), ("filtered", ctypes.c_void_p)]
 
 
+class Crop(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_int), ("y", ctypes.c_int), ("x", ctypes.c_int), ("scale", ctypes.c_int)]
+
+
+class TrainingRequest(ctypes.Structure):
+    _fields_ = [("n_sources", ctypes.c_int), ("sources", ctypes.c_void_p), ("source_H", ctypes.c_void_p),
+                ("source_W", ctypes.c_void_p), ("n_crops", ctypes.c_int), ("crops", ctypes.c_void_p),
+                ("size", ctypes.c_int), ("standardize", ctypes.c_int), ("mean_std", ctypes.c_double * 2),
+                ("dt", ctypes.c_double), ("K", ctypes.c_int), ("n_inner", ctypes.c_int),
+                ("band_edges", ctypes.c_void_p), ("n_edges", ctypes.c_int), ("crops_out", ctypes.c_void_p),
+                ("bands", ctypes.c_void_p), ("residual", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("stats", ctypes.c_void_p), ("mem_kind", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
                 ("graphs_built", ctypes.c_uint64), ("decompositions", ctypes.c_uint64),
@@ -77,6 +91,7 @@ _SIGS = {
                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_void_p]),
     "tvspec_decompose_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_void_p]),
+    "tvspec_training_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TrainingRequest), ctypes.c_void_p]),
     "tvspec_decompose_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Request),
                                               ctypes.c_void_p]),
     "tvspec_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -305,6 +320,63 @@ class Plan:
         st = _stream_ptr(stream) if MEM_DEVICE in kinds else None
         _check(self._lib.tvspec_decompose_batch(self._h, len(reqs), arr, st), "tvspec_decompose_batch")
         return outs
+
+    # ---- training-data generation (Sec. 4.1) ---------------------------------------------------
+    def training_set(self, sources, crops, size: int, standardize: int, dt: float, K: int, n_inner: int,
+                     edges, mean_std=(0.0, 1.0), want_crops: bool = True, want_stats: bool = True,
+                     stream=None) -> Result:
+        """Crops (src, y, x, scale) of the sources, standardised (0 none, 1 over the crops,
+        2 per crop, 3 by mean_std) and decomposed. Host (numpy) or CUDA (torch) sources; the
+        Result holds ``crops`` (n, size, size), ``bands`` (n, n_bands, size, size),
+        ``residual`` (n, size, size), ``S`` (n, K-1) and ``stats`` (host float64)."""
+        e = self._edges(edges)
+        nb = len(e) - 1
+        n = len(crops)
+        device = all(_is_torch_cuda(x) for x in sources) and len(sources) > 0
+        if device:
+            import torch
+
+            srcs = [x.contiguous() for x in sources]
+            for x in srcs:
+                if x.dtype != torch.float32 or x.dim() != 2:
+                    raise TypeError("sources must be 2-D float32 tensors")
+            dev = srcs[0].device
+            mk = lambda *shape, dt=torch.float32: torch.empty(shape, dtype=dt, device=dev)
+            out = Result(bands=mk(n, nb, size, size), residual=mk(n, size, size),
+                         S=mk(n, max(K - 1, 0), dt=torch.float64))
+            if want_crops:
+                out["crops"] = mk(n, size, size)
+            ptr = lambda t: t.data_ptr()
+            kind = MEM_DEVICE
+        else:
+            srcs = [np.ascontiguousarray(np.asarray(x, np.float32)) for x in sources]
+            if any(x.ndim != 2 for x in srcs):
+                raise TypeError("sources must be 2-D")
+            out = Result(bands=np.zeros((n, nb, size, size), np.float32), residual=np.zeros((n, size, size), np.float32),
+                         S=np.zeros((n, max(K - 1, 0)), np.float64))
+            if want_crops:
+                out["crops"] = np.zeros((n, size, size), np.float32)
+            ptr = lambda a: a.ctypes.data
+            kind = MEM_HOST
+        ptrs = (ctypes.c_void_p * len(srcs))(*[ptr(x) for x in srcs])
+        hs = np.ascontiguousarray([x.shape[0] for x in srcs], np.int32)
+        ws = np.ascontiguousarray([x.shape[1] for x in srcs], np.int32)
+        ca = (Crop * max(n, 1))(*[Crop(int(c[0]), int(c[1]), int(c[2]), int(c[3])) for c in crops])
+        stats = np.zeros(max(2, 2 * n) if standardize == 2 else 2, np.float64)
+        r = TrainingRequest(n_sources=len(srcs), sources=ctypes.cast(ptrs, ctypes.c_void_p),
+                            source_H=hs.ctypes.data, source_W=ws.ctypes.data, n_crops=n,
+                            crops=ctypes.cast(ca, ctypes.c_void_p), size=int(size), standardize=int(standardize),
+                            dt=float(dt), K=int(K), n_inner=int(n_inner), band_edges=e.ctypes.data,
+                            n_edges=len(e), crops_out=ptr(out["crops"]) if want_crops else None,
+                            bands=ptr(out["bands"]), residual=ptr(out["residual"]),
+                            S=ptr(out["S"]) if K > 1 else ptr(out["residual"]),
+                            stats=stats.ctypes.data if want_stats else None, mem_kind=kind)
+        r.mean_std[0], r.mean_std[1] = float(mean_std[0]), float(mean_std[1])
+        st = _stream_ptr(stream) if kind == MEM_DEVICE else None
+        _check(self._lib.tvspec_training_set(self._h, ctypes.byref(r), st), "tvspec_training_set")
+        if want_stats:
+            out["stats"] = stats[:2 * n] if standardize == 2 else stats[:2]
+        return out
 
     # ---- serving -------------------------------------------------------------------------------
     def submit(self, f, dt, K, n_inner, edges, trace: bool = False, filters=None):

@@ -580,8 +580,7 @@ static std::string job_key(const tvspec_config &c, const std::vector<Job> &jobs)
     return k.str();
 }
 
-static tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs,
-                               CacheEntry **out) {
+tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEntry **out) {
     const std::string key = job_key(plan->cfg, jobs);
     for (auto it = plan->cache.begin(); it != plan->cache.end(); ++it) {
         if ((*it)->key == key) {
@@ -701,6 +700,31 @@ static tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs,
     return TVSPEC_OK;
 }
 
+tvspec_status launch_entry(tvspec_plan *plan, CacheEntry &E, cudaStream_t st) {
+    uint64_t nk = 0;
+    if (E.exec) {
+        TV_CK(cudaGraphLaunch(E.exec, st));
+        nk = E.graph_kernels;
+        plan->graph_launches++;
+    } else {
+        tvspec_status s = enqueue_decomposition(plan, E, st, &nk);
+        if (s != TVSPEC_OK) return s;
+    }
+    plan->kernel_launches += nk;
+    return TVSPEC_OK;
+}
+
+tvspec_status order_after(cudaStream_t later, cudaStream_t earlier) {
+    if (later == earlier) return TVSPEC_OK;
+    cudaEvent_t ev;
+    TV_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, earlier);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(later, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return fail_cuda(e, "stream ordering");
+    return TVSPEC_OK;
+}
+
 static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStream_t user_st) {
     std::lock_guard<std::mutex> lock(plan->mu);
     TV_CK(cudaSetDevice(plan->device));
@@ -726,16 +750,8 @@ static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStr
         const tvspec_request &r = jobs[E->order[i]].r;
         TV_CK(cudaMemcpyAsync(E->slots[i].f, r.f, (size_t)r.H * r.W * 4, in_kind, st));
     }
-    uint64_t nk = 0;
-    if (E->exec) {
-        TV_CK(cudaGraphLaunch(E->exec, st));
-        nk = E->graph_kernels;
-        plan->graph_launches++;
-    } else {
-        s = enqueue_decomposition(plan, *E, st, &nk);
-        if (s != TVSPEC_OK) return s;
-    }
-    plan->kernel_launches += nk;
+    s = launch_entry(plan, *E, st);
+    if (s != TVSPEC_OK) return s;
     for (int i = 0; i < n; ++i) {
         const tvspec_request &r = jobs[E->order[i]].r;
         const Slot &sl = E->slots[i];

@@ -136,6 +136,13 @@ tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *>
 
 size_t plan_budget(const tvspec_plan *plan);
 
+// The cached workspace, tables and graph of a set of jobs (built on first use; plan->mu held).
+tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEntry **out);
+// Enqueues the whole decomposition of a cached entry on st (graph replay when captured).
+tvspec_status launch_entry(tvspec_plan *plan, CacheEntry &E, cudaStream_t st);
+// Makes `later` wait for the work enqueued on `earlier` so far.
+tvspec_status order_after(cudaStream_t later, cudaStream_t earlier);
+
 // Tile choice for an H x W image, tuned on plan-owned scratch buffers (takes the plan lock).
 tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *depth);
 
