@@ -89,6 +89,9 @@ typedef struct {
                                holds at least 32 such images (one CTA per image needs many images
                                to fill the GPU), 2 always, 0 never; with kernel = AUTO and fp32
                                storage of p */
+    int resident_variant;   /* thread layout of the resident kernel: -1 (default) automatic,
+                               else an index below tvspec_resident_variant_count(); an image the
+                               variant cannot hold uses the automatic choice */
 } tvspec_config;
 
 /* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in
@@ -292,6 +295,13 @@ tvspec_status tvspec_decompose_noalloc(const float *f, int H, int W, double dt, 
 int tvspec_tile_count(void);
 tvspec_status tvspec_tile_info(int index, int *cols_per_lane, int *rows_per_thread, int *warps,
                                int *max_temporal_block);
+
+/* Number of thread layouts of the resident small-image kernel, and the geometry of layout
+ * `index`: the largest image it holds (max_H x max_W), threads per CTA and the CTAs per SM its
+ * register budget is built for. Returns EINVAL for an index out of range. */
+int tvspec_resident_variant_count(void);
+tvspec_status tvspec_resident_variant_info(int index, int *max_H, int *max_W, int *threads,
+                                           int *min_ctas_per_sm);
 
 /* Counters of this plan (see tvspec_stats). */
 tvspec_status tvspec_plan_stats(tvspec_plan *plan, tvspec_stats *out);

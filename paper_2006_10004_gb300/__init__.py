@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("fast_math", ctypes.c_int),
                 ("mem_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("pdl", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
-                ("test_barrier_noshow", ctypes.c_int), ("resident", ctypes.c_int)]
+                ("test_barrier_noshow", ctypes.c_int), ("resident", ctypes.c_int),
+                ("resident_variant", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -91,6 +92,8 @@ _SIGS = {
                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_void_p]),
     "tvspec_decompose_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_void_p]),
+    "tvspec_resident_variant_count": (ctypes.c_int, []),
+    "tvspec_resident_variant_info": (ctypes.c_int, [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4),
     "tvspec_training_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TrainingRequest), ctypes.c_void_p]),
     "tvspec_decompose_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Request),
                                               ctypes.c_void_p]),
@@ -160,6 +163,18 @@ def tile_shapes() -> list:
         _check(L.tvspec_tile_info(i, ctypes.byref(v), ctypes.byref(r), ctypes.byref(w), ctypes.byref(tb)),
                "tvspec_tile_info")
         out.append({"V": v.value, "R": r.value, "RW": w.value, "TB": tb.value})
+    return out
+
+
+def resident_variants() -> list:
+    """Thread layouts of the resident small-image kernel: largest image, threads, CTAs per SM."""
+    L = load()
+    out = []
+    for i in range(L.tvspec_resident_variant_count()):
+        h, w, t, m = (ctypes.c_int() for _ in range(4))
+        _check(L.tvspec_resident_variant_info(i, ctypes.byref(h), ctypes.byref(w), ctypes.byref(t),
+                                              ctypes.byref(m)), "tvspec_resident_variant_info")
+        out.append({"max_H": h.value, "max_W": w.value, "threads": t.value, "min_ctas_per_sm": m.value})
     return out
 
 

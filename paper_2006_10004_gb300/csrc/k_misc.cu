@@ -1,5 +1,7 @@
 // Kernels around the hot loop: the reference one-iteration kernel, the start of a
 // decomposition, the per-step float64 epilogue and the standalone ROF helpers.
+#include <algorithm>
+
 #include "chambolle_math.cuh"
 #include "epilogue.cuh"
 #include "tvspec_internal.h"
@@ -250,6 +252,53 @@ cudaError_t launch_rof_primal(const float *p1, const float *p2, int pitch, const
                               float *u, int H, int W, double lambda, cudaStream_t st) {
     dim3 grid((W + 255) / 256, H);
     k_rof_primal<<<grid, 256, 0, st>>>(p1, p2, pitch, g, u, H, W, lambda);
+    return cudaGetLastError();
+}
+
+}  // namespace tvspec
+
+// ---------------------------------------------------------------------------------------------
+// Copy list: many device-to-device copies in one launch. Block b copies chunk
+// b - first[i] of item i (first[] = prefix sums of the items' chunk counts).
+// ---------------------------------------------------------------------------------------------
+namespace tvspec {
+
+__global__ void __launch_bounds__(256)
+    k_copy_list(const CopyItem *__restrict__ items, const unsigned *__restrict__ first, int n,
+                unsigned n_chunks) {
+    for (unsigned b = blockIdx.x; b < n_chunks; b += gridDim.x) {
+        int lo = 0, hi = n - 1;  // last item with first[i] <= b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        const CopyItem it = items[lo];
+        const size_t begin = (size_t)(b - first[lo]) * kCopyChunk;
+        const size_t end = min(it.bytes, begin + kCopyChunk);
+        const char *s = static_cast<const char *>(it.src);
+        char *d = static_cast<char *>(it.dst);
+        if ((((uintptr_t)s | (uintptr_t)d) & 15) == 0) {
+            const size_t v_end = begin + ((end - begin) & ~(size_t)15);
+            for (size_t o = begin + 16 * threadIdx.x; o < v_end; o += 16 * blockDim.x)
+                *reinterpret_cast<int4 *>(d + o) = *reinterpret_cast<const int4 *>(s + o);
+            for (size_t o = v_end + threadIdx.x; o < end; o += blockDim.x) d[o] = s[o];
+        } else if ((((uintptr_t)s | (uintptr_t)d) & 3) == 0) {
+            const size_t v_end = begin + ((end - begin) & ~(size_t)3);
+            for (size_t o = begin + 4 * threadIdx.x; o < v_end; o += 4 * blockDim.x)
+                *reinterpret_cast<unsigned *>(d + o) = *reinterpret_cast<const unsigned *>(s + o);
+            for (size_t o = v_end + threadIdx.x; o < end; o += blockDim.x) d[o] = s[o];
+        } else {
+            for (size_t o = begin + threadIdx.x; o < end; o += blockDim.x) d[o] = s[o];
+        }
+    }
+}
+
+cudaError_t launch_copy_list(const CopyItem *items, const unsigned *first, int n,
+                             unsigned n_chunks, cudaStream_t st) {
+    if (n <= 0 || n_chunks == 0) return cudaSuccess;
+    const unsigned grid = std::min<unsigned>(n_chunks, 152u * 16u);
+    k_copy_list<<<grid, 256, 0, st>>>(items, first, n, n_chunks);
     return cudaGetLastError();
 }
 

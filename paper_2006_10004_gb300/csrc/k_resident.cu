@@ -14,8 +14,8 @@
 
 namespace tvspec {
 
-template <int V, int R, int RW, bool FAST>
-__global__ void __launch_bounds__(32 * RW, 1)
+template <int V, int R, int RW, int MINB, bool FAST>
+__global__ void __launch_bounds__(32 * RW, MINB)
     k_resident(const ImgDesc *__restrict__ descs, const int *__restrict__ idx, float tau,
                int warm_start) {
     static_assert(RW % 8 == 0, "the S reduction works in groups of 8 warps");
@@ -38,6 +38,12 @@ __global__ void __launch_bounds__(32 * RW, 1)
     const int ry = wy * R;
     float *gp1 = static_cast<float *>(d.p1[0]);
     float *gp2 = static_cast<float *>(d.p2[0]);
+
+    // this kernel clears what it needs itself (the host skips the workspace memset): the
+    // status word and the bands (a band without any t_k stays zero)
+    if (threadIdx.x == 0) *d.status = 0u;
+    for (size_t q = threadIdx.x; q < (size_t)d.n_bands * H * W; q += blockDim.x) d.bands[q] = 0.0f;
+    __syncthreads();
 
     // border masks: the tile is the image, every tile pixel outside it stays zero
     unsigned m1 = 0u, m2 = 0u;
@@ -177,31 +183,57 @@ __global__ void __launch_bounds__(32 * RW, 1)
     }
 }
 
-// Variants: (V, R, RW) -> image tile (32 V) x (RW R).
+// Variants: (V, R, RW, MINB) -> image tile (32 V) x (RW R), CTAs per SM the registers are
+// budgeted for. The automatic choice takes the first variant in kAutoOrder that holds the image.
 using ResidentKernel = void (*)(const ImgDesc *, const int *, float, int);
 
 struct ResidentVariant {
-    int V, R, RW;
+    int V, R, RW, MINB;
     ResidentKernel fast, ieee;
 };
 
+#define TVSPEC_RESIDENT(V, R, RW, MINB) \
+    {V, R, RW, MINB, &k_resident<V, R, RW, MINB, true>, &k_resident<V, R, RW, MINB, false>}
 static const ResidentVariant kResident[] = {
-    {2, 2, 32, &k_resident<2, 2, 32, true>, &k_resident<2, 2, 32, false>},  //  64 x  64
-    {2, 4, 32, &k_resident<2, 4, 32, true>, &k_resident<2, 4, 32, false>},  //  64 x 128
-    {4, 2, 32, &k_resident<4, 2, 32, true>, &k_resident<4, 2, 32, false>},  // 128 x  64
+    TVSPEC_RESIDENT(2, 2, 32, 1),  // 0:  64 x  64, 1024 threads, 4 px each
+    TVSPEC_RESIDENT(2, 4, 32, 1),  // 1: 128 x  64 (H x W)
+    TVSPEC_RESIDENT(4, 2, 32, 1),  // 2:  64 x 128
+    TVSPEC_RESIDENT(2, 8, 8, 2),   // 3:  64 x  64,  256 threads, 16 px each, 2 CTAs / SM
+    TVSPEC_RESIDENT(2, 4, 16, 1),  // 4:  64 x  64,  512 threads, 8 px each
+    TVSPEC_RESIDENT(2, 4, 16, 2),  // 5:  64 x  64,  512 threads, 2 CTAs / SM
+    TVSPEC_RESIDENT(2, 8, 8, 3),   // 6:  64 x  64,  256 threads, 3 CTAs / SM
+    TVSPEC_RESIDENT(2, 8, 8, 4),   // 7:  64 x  64,  256 threads, 4 CTAs / SM
 };
+#undef TVSPEC_RESIDENT
+static constexpr int kNumResident = (int)(sizeof(kResident) / sizeof(kResident[0]));
+static const int kAutoOrder[] = {6, 1, 2};
 
-int resident_variant_for(int H, int W) {
-    for (int i = 0; i < (int)(sizeof(kResident) / sizeof(kResident[0])); ++i)
-        if (W <= 32 * kResident[i].V && H <= kResident[i].RW * kResident[i].R && W <= 256 &&
-            H <= 256)
-            return i;
+static bool resident_holds(int i, int H, int W) {
+    return W <= 32 * kResident[i].V && H <= kResident[i].RW * kResident[i].R;
+}
+
+int resident_variant_count() { return kNumResident; }
+
+bool resident_variant_info(int i, int *max_h, int *max_w, int *threads, int *minb) {
+    if (i < 0 || i >= kNumResident) return false;
+    *max_h = kResident[i].RW * kResident[i].R;
+    *max_w = 32 * kResident[i].V;
+    *threads = 32 * kResident[i].RW;
+    *minb = kResident[i].MINB;
+    return true;
+}
+
+int resident_variant_for(int H, int W, int preferred) {
+    if (preferred >= 0 && preferred < kNumResident && resident_holds(preferred, H, W)) return preferred;
+    for (int i : kAutoOrder)
+        if (resident_holds(i, H, W)) return i;
     return -1;
 }
 
 cudaError_t launch_resident(int variant, bool fast, const ImgDesc *descs, const int *idx, int n,
                             float tau, int warm_start, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+    if (variant < 0 || variant >= kNumResident) return cudaErrorInvalidValue;
     const ResidentVariant &v = kResident[variant];
     const ResidentKernel k = fast ? v.fast : v.ieee;
     const size_t smem = (size_t)(32 * v.V) * (v.RW * v.R) * sizeof(double);

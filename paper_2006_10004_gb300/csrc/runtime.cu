@@ -524,7 +524,9 @@ static tvspec_status enqueue_decomposition(tvspec_plan *plan, CacheEntry &E, cud
                                            uint64_t *nk) {
     std::vector<Slot *> sp;
     for (Slot &s : E.slots) sp.push_back(&s);
-    for (Slot &s : E.slots) TV_CK(cudaMemsetAsync(s.base + s.zero_off, 0, s.zero_bytes, st));
+    // the resident kernel clears its own images' status and bands
+    for (int i = 0; i < E.n_tiled; ++i)
+        TV_CK(cudaMemsetAsync(E.slots[i].base + E.slots[i].zero_off, 0, E.slots[i].zero_bytes, st));
     // resident images: their whole decomposition, one launch per variant
     int off = 0;
     for (auto &g : E.res_groups) {
@@ -606,7 +608,7 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
     if (resident_ok) {
         int eligible = 0;
         for (int i = 0; i < n; ++i) {
-            variant[i] = resident_variant_for(jobs[i].r.H, jobs[i].r.W);
+            variant[i] = resident_variant_for(jobs[i].r.H, jobs[i].r.W, cf.resident_variant);
             eligible += variant[i] >= 0;
         }
         // one CTA per image only pays off when there are enough images to fill the GPU
@@ -700,6 +702,35 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
     return TVSPEC_OK;
 }
 
+tvspec_status enqueue_copy_list(const std::vector<CopyItem> &items, cudaStream_t st) {
+    std::vector<CopyItem> it;
+    for (const CopyItem &c : items)
+        if (c.bytes > 0) it.push_back(c);
+    if (it.empty()) return TVSPEC_OK;
+    const int n = (int)it.size();
+    std::vector<unsigned> first(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        first[i] = (unsigned)total;
+        total += (it[i].bytes + kCopyChunk - 1) / kCopyChunk;
+    }
+    if (total >= (size_t)UINT32_MAX) return fail(TVSPEC_EINVAL, "copy list too large");
+    const size_t o_first = ((sizeof(CopyItem) * n) + 255) & ~(size_t)255;
+    const size_t bytes = o_first + sizeof(unsigned) * n;
+    std::vector<char> host(bytes);
+    std::memcpy(host.data(), it.data(), sizeof(CopyItem) * n);
+    std::memcpy(host.data() + o_first, first.data(), sizeof(unsigned) * n);
+    char *d = nullptr;
+    TV_CK(cudaMallocAsync((void **)&d, bytes, st));
+    cudaError_t e = cudaMemcpyAsync(d, host.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_copy_list(reinterpret_cast<const CopyItem *>(d),
+                             reinterpret_cast<const unsigned *>(d + o_first), n, (unsigned)total, st);
+    cudaFreeAsync(d, st);
+    if (e != cudaSuccess) return fail_cuda(e, "copy list");
+    return TVSPEC_OK;
+}
+
 tvspec_status launch_entry(tvspec_plan *plan, CacheEntry &E, cudaStream_t st) {
     uint64_t nk = 0;
     if (E.exec) {
@@ -746,25 +777,38 @@ static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStr
     const cudaMemcpyKind in_kind = mk == TVSPEC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind out_kind = mk == TVSPEC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     const int n = (int)jobs.size();
+    // device-memory batches move their inputs and outputs with one copy-list launch each
+    const bool listed = mk == TVSPEC_MEM_DEVICE && n >= 2;
+    std::vector<CopyItem> cin, cout;
     for (int i = 0; i < n; ++i) {
         const tvspec_request &r = jobs[E->order[i]].r;
-        TV_CK(cudaMemcpyAsync(E->slots[i].f, r.f, (size_t)r.H * r.W * 4, in_kind, st));
+        const size_t bytes = (size_t)r.H * r.W * 4;
+        if (listed) cin.push_back({r.f, E->slots[i].f, bytes});
+        else TV_CK(cudaMemcpyAsync(E->slots[i].f, r.f, bytes, in_kind, st));
     }
+    s = enqueue_copy_list(cin, st);
+    if (s != TVSPEC_OK) return s;
     s = launch_entry(plan, *E, st);
     if (s != TVSPEC_OK) return s;
     for (int i = 0; i < n; ++i) {
         const tvspec_request &r = jobs[E->order[i]].r;
         const Slot &sl = E->slots[i];
         const size_t N = (size_t)r.H * r.W;
-        TV_CK(cudaMemcpyAsync(r.bands, sl.bands, (size_t)sl.n_bands * N * 4, out_kind, st));
-        TV_CK(cudaMemcpyAsync(r.residual, sl.residual, N * 4, out_kind, st));
-        TV_CK(cudaMemcpyAsync(r.S, sl.S, (size_t)(r.K - 1) * 8, out_kind, st));
-        if (r.u_trace)
-            TV_CK(cudaMemcpyAsync(r.u_trace, sl.utrace, (size_t)(r.K + 1) * N * 8, out_kind, st));
-        if (r.n_filters > 0)
-            TV_CK(cudaMemcpyAsync(r.filtered, sl.filtered, (size_t)r.n_filters * N * 4, out_kind, st));
-        TV_CK(cudaMemcpyAsync(E->h_status + i, sl.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        const CopyItem out[] = {{sl.bands, r.bands, (size_t)sl.n_bands * N * 4},
+                                {sl.residual, r.residual, N * 4},
+                                {sl.S, r.S, (size_t)(r.K - 1) * 8},
+                                {sl.utrace, r.u_trace, r.u_trace ? (size_t)(r.K + 1) * N * 8 : 0},
+                                {sl.filtered, r.filtered, (size_t)r.n_filters * N * 4}};
+        for (const CopyItem &c : out) {
+            if (c.bytes == 0) continue;
+            if (listed) cout.push_back(c);
+            else TV_CK(cudaMemcpyAsync(c.dst, c.src, c.bytes, out_kind, st));
+        }
+        if (mk == TVSPEC_MEM_HOST)
+            TV_CK(cudaMemcpyAsync(E->h_status + i, sl.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     }
+    s = enqueue_copy_list(cout, st);
+    if (s != TVSPEC_OK) return s;
     if (user_st) {
         // later work on the plan stream must see this call's use of the workspace
         cudaEvent_t ev;
@@ -917,6 +961,7 @@ void tvspec_config_init(tvspec_config *cfg) {
     cfg->barrier_timeout_ms = 2000;
     cfg->test_barrier_noshow = -1;
     cfg->resident = 1;
+    cfg->resident_variant = -1;
 }
 
 tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_plan **out) {
@@ -933,6 +978,8 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
     if (c.max_batch < 0) return fail(TVSPEC_EINVAL, "max_batch must be >= 0");
     if (c.barrier_timeout_ms < 1) return fail(TVSPEC_EINVAL, "barrier_timeout_ms must be >= 1");
     if (c.resident < 0 || c.resident > 2) return fail(TVSPEC_EINVAL, "resident must be 0, 1 or 2");
+    if (c.resident_variant < -1 || c.resident_variant >= resident_variant_count())
+        return fail(TVSPEC_EINVAL, "resident_variant out of range");
     int n_dev = 0;
     cudaError_t e = cudaGetDeviceCount(&n_dev);
     if (e != cudaSuccess || n_dev == 0) {
@@ -1124,6 +1171,20 @@ tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float
         TV_CK(cudaMemcpyAsync(p1, d.p1[1], pb, cudaMemcpyDeviceToDevice, st));
         TV_CK(cudaMemcpyAsync(p2, d.p2[1], pb, cudaMemcpyDeviceToDevice, st));
     }
+    return TVSPEC_OK;
+}
+
+int tvspec_resident_variant_count(void) { return resident_variant_count(); }
+
+tvspec_status tvspec_resident_variant_info(int index, int *max_H, int *max_W, int *threads,
+                                           int *min_ctas_per_sm) {
+    int h, w, t, m;
+    if (!resident_variant_info(index, &h, &w, &t, &m))
+        return fail(TVSPEC_EINVAL, "resident variant index out of range");
+    if (max_H) *max_H = h;
+    if (max_W) *max_W = w;
+    if (threads) *threads = t;
+    if (min_ctas_per_sm) *min_ctas_per_sm = m;
     return TVSPEC_OK;
 }
 

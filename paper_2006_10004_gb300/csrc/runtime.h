@@ -140,6 +140,8 @@ size_t plan_budget(const tvspec_plan *plan);
 tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEntry **out);
 // Enqueues the whole decomposition of a cached entry on st (graph replay when captured).
 tvspec_status launch_entry(tvspec_plan *plan, CacheEntry &E, cudaStream_t st);
+// Device-to-device copies as one launch (stream-ordered table; zero-byte items skipped).
+tvspec_status enqueue_copy_list(const std::vector<CopyItem> &items, cudaStream_t st);
 // Makes `later` wait for the work enqueued on `earlier` so far.
 tvspec_status order_after(cudaStream_t later, cudaStream_t earlier);
 

@@ -120,7 +120,9 @@ cudaError_t launch_step_coop(int shape, bool fast, const ImgDesc &d, int gstep, 
 
 // Resident small-image kernel: the whole decomposition of each image idx[0..n) of descs in
 // one CTA (fp32). resident_variant_for gives the variant whose tile holds an H x W image, or -1.
-int resident_variant_for(int H, int W);
+int resident_variant_for(int H, int W, int preferred = -1);
+int resident_variant_count();
+bool resident_variant_info(int i, int *max_h, int *max_w, int *threads, int *minb);
 cudaError_t launch_resident(int variant, bool fast, const ImgDesc *descs, const int *idx, int n,
                             float tau, int warm_start, cudaStream_t st);
 
@@ -153,6 +155,17 @@ cudaError_t launch_epilogue_one(int p_storage, const ImgDesc &d, int gstep, int 
 // inputs, float32 output, compact layout for u and g, pitched p).
 cudaError_t launch_rof_primal(const float *p1, const float *p2, int pitch, const float *g,
                               float *u, int H, int W, double lambda, cudaStream_t st);
+
+// Many device-to-device copies in one launch: items[i] copies bytes from src to dst; first[i]
+// is the index of item i's first chunk of kCopyChunk bytes (prefix sums), n_chunks the total.
+struct CopyItem {
+    const void *src;
+    void *dst;
+    size_t bytes;
+};
+constexpr size_t kCopyChunk = 16384;
+cudaError_t launch_copy_list(const CopyItem *items, const unsigned *first, int n,
+                             unsigned n_chunks, cudaStream_t st);
 
 // Pitched copies between compact float images and pitched workspace arrays.
 cudaError_t launch_gl_from_g(const float *g, float *gl, int H, int W, int pitch, double lambda,

@@ -79,6 +79,15 @@ def test_validate_rejects_non_finite_host_image():
     assert tv.validate((4, 4), 0.5, 4, 10, (0, INF), f=f) == tv.EINVAL
 
 
+def test_resident_variant_table():
+    vs = tv.resident_variants()
+    assert len(vs) >= 3
+    assert {(v["max_H"], v["max_W"]) for v in vs} >= {(64, 64), (128, 64), (64, 128)}
+    for v in vs:
+        assert v["threads"] % 256 == 0 and v["threads"] <= 1024 and v["min_ctas_per_sm"] >= 1
+    assert tv.load().tvspec_resident_variant_info(len(vs), None, None, None, None) == tv.EINVAL
+
+
 def test_validate_filters():
     K = 6
     ok = [(np.ones(K - 1), 1.0), (np.linspace(0, 1, K - 1), 0.0)]

@@ -155,6 +155,19 @@ def test_resident_small_image_kernel_bit_identical(tv, H, W, warm):
     assert_parity(ra, ref, f, f"resident {H}x{W}")
 
 
+def test_every_resident_variant_bit_identical(tv):
+    # every thread layout of the resident kernel that holds the image gives the per-step bits
+    shapes = [(64, 64), (33, 50), (7, 64), (64, 5), (120, 60), (60, 120)]
+    imgs = {s: _img(*s, seed=13 * s[0] + s[1]) for s in shapes}
+    with tv.Plan(0, resident=0) as b:
+        want = {s: b.decompose(f, 0.5, 5, 23, syn.DYADIC_EDGES, trace=True) for s, f in imgs.items()}
+    for v, info in enumerate(tv.resident_variants()):
+        with tv.Plan(0, resident=2, resident_variant=v) as a:
+            for s, f in imgs.items():
+                if s[0] <= info["max_H"] and s[1] <= info["max_W"]:
+                    _same(a.decompose(f, 0.5, 5, 23, syn.DYADIC_EDGES, trace=True), want[s])
+
+
 def test_resident_batch_of_crops(tv):
     # the training-data use: many 64^2 crops, K = 50, dyadic bands, in one launch (the default
     # chooses the resident kernel from 32 eligible images on)
@@ -218,6 +231,29 @@ def test_batch_matches_alone_bit_identical_and_oracle(plan):
         _same(out, alone)
         ref = oracle.decompose(*job, trace=True)
         assert_parity(out, ref, job[0])
+
+
+def test_device_batch_copy_list_matches_host_batch(plan):
+    # device batches move inputs and outputs with one copy-list launch each; the inputs here are
+    # views into one flat buffer at offsets that are not 16-byte aligned
+    import torch
+
+    rng = np.random.default_rng(12)
+    imgs = [_img(int(rng.integers(5, 90)), int(rng.integers(5, 90)), 200 + j) for j in range(9)]
+    flat = torch.zeros(sum(x.size for x in imgs) + 3 * len(imgs) + 1, dtype=torch.float32, device="cuda")
+    views, off = [], 1
+    for x in imgs:
+        v = flat[off:off + x.size].view(x.shape)
+        v.copy_(torch.from_numpy(x))
+        views.append(v)
+        off += x.size + 3
+    bank = [(np.linspace(0.0, 1.0, 4), 0.5)]
+    host = plan.decompose_batch([(x, 0.5, 5, 20, syn.DYADIC_EDGES, bank) for x in imgs], trace=True)
+    dev = plan.decompose_batch([(v, 0.5, 5, 20, syn.DYADIC_EDGES, bank) for v in views], trace=True)
+    torch.cuda.synchronize()
+    for h, d in zip(host, dev):
+        for k in ("bands", "residual", "S", "u", "filtered"):
+            assert np.array_equal(h[k], d[k].cpu().numpy()), k
 
 
 # ---------------------------------------------------------------------------------------------
