@@ -77,6 +77,8 @@ def _lib():
             h.orc_decompose.restype = ctypes.c_int
             h.orc_decompose_filtered.argtypes = h.orc_decompose.argtypes + [ctypes.c_int, _dp, _dp, _dp]
             h.orc_decompose_filtered.restype = ctypes.c_int
+            h.orc_decompose_full.argtypes = h.orc_decompose_filtered.argtypes + [_dp]
+            h.orc_decompose_full.restype = ctypes.c_int
             h.orc_crop.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, _dp]
             h.orc_crop.restype = ctypes.c_int
@@ -156,8 +158,9 @@ def decompose(f, dt: float, K: int, n_inner: int, edges, tau: float = 0.125,
               warm_start: bool = True, trace: bool = False, filters=None) -> dict:
     """Spectral TV decomposition of ``f`` (H x W).
 
-    Returns a dict with ``bands`` ((n_edges-1, H, W)), ``residual`` ((H, W)), ``S`` ((K-1,))
-    and, when ``trace`` is set, ``u`` ((K+1, H, W)) holding u_0..u_K. All float64.
+    Returns a dict with ``bands`` ((n_edges-1, H, W)), ``residual`` ((H, W)), ``S`` ((K-1,)),
+    ``S_parseval`` ((K-1,), <phi_k, f>) and, when ``trace`` is set, ``u`` ((K+1, H, W)) holding
+    u_0..u_K. All float64.
     ``filters``: optional list of (H_values, h_r) with H_values[k-1] = H(t_k) for k=1..K-1;
     adds ``filtered`` ((n_filters, H, W)) = sum_k H(t_k) phi_k dt + h_r f_r (Eq. filteredTVtrafo).
     """
@@ -175,15 +178,16 @@ def decompose(f, dt: float, K: int, n_inner: int, edges, tau: float = 0.125,
     fH = _f64([np.asarray(h, np.float64).reshape(K - 1) for h, _ in filters]) if nf else np.zeros(1)
     fr = _f64([r for _, r in filters]) if nf else np.zeros(1)
     filtered = np.zeros((max(nf, 1), H, W))
-    rc = _lib().orc_decompose_filtered(_ptr(f), H, W, float(dt), int(K), int(n_inner), float(tau),
-                                       1 if warm_start else 0, _ptr(e), len(e), _ptr(bands),
-                                       _ptr(residual), _ptr(S), _ptr(ut) if trace else None,
-                                       nf, _ptr(fH), _ptr(fr), _ptr(filtered))
+    S_par = np.zeros(max(K - 1, 0))
+    rc = _lib().orc_decompose_full(_ptr(f), H, W, float(dt), int(K), int(n_inner), float(tau),
+                                   1 if warm_start else 0, _ptr(e), len(e), _ptr(bands),
+                                   _ptr(residual), _ptr(S), _ptr(ut) if trace else None,
+                                   nf, _ptr(fH), _ptr(fr), _ptr(filtered), _ptr(S_par))
     if rc == -2:
         raise ValueError("oracle: invalid arguments")
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
-    out = {"bands": bands, "residual": residual, "S": S}
+    out = {"bands": bands, "residual": residual, "S": S, "S_parseval": S_par}
     if nf:
         out["filtered"] = filtered
     if trace:

@@ -18,6 +18,7 @@
  *   - the residual f_r(T) = u(T) - T u_t(T)                                   (Eq. finite_inverse_trafo)
  *   - filtered images f_H = int_0^T phi(t) H(t) dt + h_r f_r                  (Eq. filteredTVtrafo
  *     substituted into Eq. finite_inverse_trafo; h_r weighs the residual)
+ *   - a Parseval-type spectrum <phi(t), f>                                    (Sec. 2.1 names it)
  *
  * Readings of points the paper leaves open (each one is listed in the design notes):
  *   - forward differences with a zero last row/column (Neumann), divergence = -grad^T;
@@ -194,13 +195,17 @@ int orc_band_of(double t, const double *edges, int n_edges)
  *   filters  n_filters filters: filter_H[q*(K-1) + k-1] = H_q(t_k), filter_res[q] = h_r of
  *            filter q; filtered (n_filters*H*W) receives
  *            f_Hq = sum_{k=1}^{K-1} H_q(t_k) phi_k dt + h_r f_r  (Riemann sum, as the bands)
+ *   S_par    K-1 values of the Parseval-type spectrum S_par[k-1] = <phi_k, f> = sum_ij
+ *            phi_k(i,j) f(i,j), or NULL. The paper only names this alternative (Burger et al.
+ *            2016, cited in Sec. 2.1); read here as the pairing of phi with f, for which
+ *            sum_k <phi_k, f> dt + <f_r, f> = |f|^2 follows from the reconstruction.
  * Returns 0, -1 on allocation failure, -2 on invalid arguments.
  */
-int orc_decompose_filtered(const double *f, int H, int W, double dt, int K, int n_inner,
-                           double tau, int warm_start, const double *edges, int n_edges,
-                           double *bands, double *residual, double *S, double *u_trace,
-                           int n_filters, const double *filter_H, const double *filter_res,
-                           double *filtered)
+int orc_decompose_full(const double *f, int H, int W, double dt, int K, int n_inner,
+                       double tau, int warm_start, const double *edges, int n_edges,
+                       double *bands, double *residual, double *S, double *u_trace,
+                       int n_filters, const double *filter_H, const double *filter_res,
+                       double *filtered, double *S_par)
 {
     if (H < 1 || W < 1 || K < 2 || n_inner < 0 || !(dt > 0.0) || n_edges < 2)
         return -2;
@@ -239,10 +244,11 @@ int orc_decompose_filtered(const double *f, int H, int W, double dt, int K, int 
             /* phi_k = t_k u_tt(t_k) by the central second difference (Eq. TVtrafo) */
             double t_k = (double)k * dt;
             int m = orc_band_of(t_k, edges, n_edges);
-            double s = 0.0;
+            double s = 0.0, sp = 0.0;
             for (size_t n = 0; n < N; ++n) {
                 double phi = t_k * (u_next[n] - 2.0 * u_cur[n] + u_prev[n]) / (dt * dt);
                 s += fabs(phi);                              /* S(t) = |phi(t)|_L1 */
+                sp += phi * f[n];                            /* <phi(t), f> */
                 if (m >= 0)
                     bands[(size_t)m * N + n] += phi * dt;    /* Eq. spectral_bands */
                 for (int q = 0; q < n_filters; ++q)          /* Eq. filteredTVtrafo */
@@ -250,6 +256,8 @@ int orc_decompose_filtered(const double *f, int H, int W, double dt, int K, int 
                         filter_H[(size_t)q * (K - 1) + (k - 1)] * phi * dt;
             }
             S[k - 1] = s;
+            if (S_par)
+                S_par[k - 1] = sp;
         }
         double *tmp = u_prev;
         u_prev = u_cur;
@@ -268,6 +276,18 @@ int orc_decompose_filtered(const double *f, int H, int W, double dt, int K, int 
     }
     free(u_prev); free(u_cur); free(u_next); free(p1); free(p2);
     return rc;
+}
+
+/* The decomposition with filters, without the Parseval-type spectrum. */
+int orc_decompose_filtered(const double *f, int H, int W, double dt, int K, int n_inner,
+                           double tau, int warm_start, const double *edges, int n_edges,
+                           double *bands, double *residual, double *S, double *u_trace,
+                           int n_filters, const double *filter_H, const double *filter_res,
+                           double *filtered)
+{
+    return orc_decompose_full(f, H, W, dt, K, n_inner, tau, warm_start, edges, n_edges, bands,
+                              residual, S, u_trace, n_filters, filter_H, filter_res, filtered,
+                              NULL);
 }
 
 /* The decomposition without filters. */

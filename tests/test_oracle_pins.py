@@ -379,3 +379,41 @@ def test_filtering_is_one_homogeneous_exactly():
     a = oracle.decompose(f, dt, K, 40, syn.DYADIC_EDGES, filters=[(h, 0.5)])
     b = oracle.decompose(2 * f, 2 * dt, K, 40, tuple(2 * x for x in syn.DYADIC_EDGES), filters=[(h, 0.5)])
     assert np.array_equal(b["filtered"], 2 * a["filtered"])
+
+
+# --------------------------------------------------------------------------------------------
+# Parseval-type spectrum <phi_k, f> (the alternative spectrum Sec. 2.1 names): its Riemann sum
+# with the residual's pairing is |f|^2, each band's pairing with f is its share of that sum,
+# it is exactly one-homogeneous, and for a disk it peaks where S(t) does.
+# --------------------------------------------------------------------------------------------
+def test_parseval_spectrum_sums_to_the_energy():
+    f, dt, K, tk = _filt_setup()
+    out = oracle.decompose(f, dt, K, 40, syn.DYADIC_EDGES)
+    total = out["S_parseval"].sum() * dt + float((out["residual"] * f).sum())
+    assert abs(total - float((f * f).sum())) <= 1e-11 * float((f * f).sum())
+
+
+def test_parseval_spectrum_splits_over_the_bands():
+    f, dt, K, tk = _filt_setup()
+    e = syn.DYADIC_EDGES
+    out = oracle.decompose(f, dt, K, 40, e)
+    for m, ks in enumerate(syn.band_index_ranges(dt, K, e)):
+        want = float((out["bands"][m] * f).sum())
+        got = sum(out["S_parseval"][k - 1] for k in ks) * dt
+        assert abs(got - want) <= 1e-11 * max(1.0, abs(want)), (m, got, want)
+
+
+def test_parseval_spectrum_one_homogeneous_and_constant_image():
+    f, dt, K, tk = _filt_setup()
+    a = oracle.decompose(f, dt, K, 40, syn.DYADIC_EDGES)
+    b = oracle.decompose(2 * f, 2 * dt, K, 40, tuple(2 * x for x in syn.DYADIC_EDGES))
+    assert np.array_equal(b["S_parseval"], 2 * a["S_parseval"])
+    c = oracle.decompose(np.full((9, 7), 0.4), dt, K, 40, syn.DYADIC_EDGES)
+    assert np.all(c["S_parseval"] == 0)
+
+
+def test_parseval_spectrum_of_a_disk_peaks_with_S():
+    dt, K = 0.1, 70
+    f = syn.disk_image(48, 48, 8.0, 1.0).astype(np.float64)
+    out = oracle.decompose(f, dt, K, 300, (0.0, INF))
+    assert abs(int(np.argmax(out["S_parseval"])) - int(np.argmax(out["S"]))) <= 1
