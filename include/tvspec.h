@@ -118,6 +118,11 @@ typedef struct {
     const double *filter_H;     /* host: n_filters*(K-1) finite values, H_q(t_k) at q*(K-1) + k-1 */
     const double *filter_residual; /* host: n_filters finite weights h_q of the residual */
     float *filtered;            /* out: n_filters*H*W images (mem_kind memory) */
+    /* Parseval-type spectrum (the alternative Sec. 2.1 names, after Burger et al. 2016), read
+     * as the pairing <phi_k, f> = sum_ij phi_k(i,j) f(i,j), for which
+     * sum_k <phi_k, f> dt + <f_r, f> = |f|^2. Reduced in float64 with the same fixed
+     * partition as S. */
+    double *S_parseval;         /* out, optional (NULL): K-1 values (mem_kind memory) */
 } tvspec_request;
 
 typedef struct {

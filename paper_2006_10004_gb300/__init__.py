@@ -54,7 +54,8 @@ class Request(ctypes.Structure):
                 ("bands", ctypes.c_void_p), ("residual", ctypes.c_void_p), ("S", ctypes.c_void_p),
                 ("u_trace", ctypes.c_void_p), ("mem_kind", ctypes.c_int),
                 ("n_filters", ctypes.c_int), ("filter_H", ctypes.c_void_p),
-                ("filter_residual", ctypes.c_void_p), ("filtered", ctypes.c_void_p)]
+                ("filter_residual", ctypes.c_void_p), ("filtered", ctypes.c_void_p),
+                ("S_parseval", ctypes.c_void_p)]
 
 
 class Crop(ctypes.Structure):
@@ -251,7 +252,7 @@ class Plan:
         fr = np.ascontiguousarray(np.asarray([float(r) for _, r in filters], np.float64))
         return nf, fH, fr
 
-    def _make_request(self, f, dt, K, n_inner, edges, trace, keep, filters=None):
+    def _make_request(self, f, dt, K, n_inner, edges, trace, keep, filters=None, parseval=False):
         e = self._edges(edges)
         keep.append(e)
         nb = len(e) - 1
@@ -272,6 +273,8 @@ class Plan:
                 out["u"] = torch.empty((K + 1, H, W), dtype=torch.float64, device=dev)
             if nf:
                 out["filtered"] = torch.empty((nf, H, W), dtype=torch.float32, device=dev)
+            if parseval:
+                out["S_parseval"] = torch.empty((max(K - 1, 1),), dtype=torch.float64, device=dev)
             ptr = lambda t: t.data_ptr()
             kind = MEM_DEVICE
         else:
@@ -285,6 +288,8 @@ class Plan:
                 out["u"] = np.zeros((K + 1, H, W), np.float64)
             if nf:
                 out["filtered"] = np.zeros((nf, H, W), np.float32)
+            if parseval:
+                out["S_parseval"] = np.zeros((max(K - 1, 1),), np.float64)
             ptr = lambda a: a.ctypes.data
             kind = MEM_HOST
         keep.append(f)
@@ -294,18 +299,20 @@ class Plan:
                     u_trace=ptr(out["u"]) if trace else None, mem_kind=kind, n_filters=nf,
                     filter_H=fH.ctypes.data if nf else None,
                     filter_residual=fr.ctypes.data if nf else None,
-                    filtered=ptr(out["filtered"]) if nf else None)
+                    filtered=ptr(out["filtered"]) if nf else None,
+                    S_parseval=ptr(out["S_parseval"]) if parseval else None)
         return r, out, kind
 
     def decompose(self, f, dt: float, K: int, n_inner: int, edges, trace: bool = False, stream=None,
-                  filters=None):
+                  filters=None, parseval: bool = False):
         """Decompose one image; returns a Result (numpy for host input, torch for CUDA input).
 
         ``filters``: optional list of (H_values, h_r) spectral filters (Eq. filteredTVtrafo);
-        the Result then holds ``filtered`` ((n_filters, H, W)).
+        the Result then holds ``filtered`` ((n_filters, H, W)). ``parseval`` adds ``S_parseval``
+        ((K-1,), the Parseval-type spectrum <phi_k, f>).
         """
         keep = []
-        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep, filters)
+        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep, filters, parseval)
         st = _stream_ptr(stream) if kind == MEM_DEVICE else None
         _check(self._lib.tvspec_decompose_ex(self._h, ctypes.byref(r), st), "tvspec_decompose_ex")
         return out
@@ -318,14 +325,14 @@ class Plan:
                                           len(e), bands_ptr, residual_ptr, S_ptr, mem_kind, stream),
                "tvspec_decompose")
 
-    def decompose_batch(self, jobs, trace: bool = False, stream=None):
+    def decompose_batch(self, jobs, trace: bool = False, stream=None, parseval: bool = False):
         """jobs: iterable of (f, dt, K, n_inner, edges[, filters]). Returns a list of Results."""
         keep = []
         reqs, outs, kinds = [], [], set()
         for job in jobs:
             f, dt, K, n_inner, edges = job[:5]
             r, o, k = self._make_request(f, dt, K, n_inner, edges, trace, keep,
-                                         job[5] if len(job) > 5 else None)
+                                         job[5] if len(job) > 5 else None, parseval)
             reqs.append(r)
             outs.append(o)
             kinds.add(k)
@@ -394,10 +401,10 @@ class Plan:
         return out
 
     # ---- serving -------------------------------------------------------------------------------
-    def submit(self, f, dt, K, n_inner, edges, trace: bool = False, filters=None):
+    def submit(self, f, dt, K, n_inner, edges, trace: bool = False, filters=None, parseval: bool = False):
         """Queue one host-memory request; returns (ticket, Result). Keep the Result alive."""
         keep = []
-        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep, filters)
+        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep, filters, parseval)
         if kind != MEM_HOST:
             raise TypeError("serving takes host (numpy) images")
         t = ctypes.c_uint64()

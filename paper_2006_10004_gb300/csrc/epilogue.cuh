@@ -22,9 +22,10 @@ __device__ __forceinline__ double div_at(int i, int j, int H, int W, float p1_ij
 //   band accumulation, band flush and residual at the last step (Eq. spectral_bands,
 //   Eq. finite_inverse_trafo), spectral filters (Eq. filteredTVtrafo); u_{k+1} replaces
 //   u_{k-1} in the ping-pong buffer.
-// Returns |phi_k| (0 at k = 0) and g/dt of the next step in *gl_next.
+// Returns |phi_k| (0 at k = 0), g/dt of the next step in *gl_next and, when the Parseval-type
+// spectrum is requested, phi_k f in *phif (0 at k = 0).
 __device__ __forceinline__ double epilogue_pixel(const ImgDesc &d, int k, size_t n, double divp,
-                                                 float *gl_next) {
+                                                 float *gl_next, double *phif) {
     const size_t N = (size_t)d.H * d.W;
     double *ucur = (k & 1) ? d.ub : d.ua;
     double *uoth = (k & 1) ? d.ua : d.ub;  // u_{k-1} in, u_{k+1} out
@@ -34,12 +35,14 @@ __device__ __forceinline__ double epilogue_pixel(const ImgDesc &d, int k, size_t
     *gl_next = (float)__dmul_rn(un, d.inv_dt);
     if (d.u_trace) d.u_trace[(size_t)(k + 1) * N + n] = un;
     double absphi = 0.0;
+    *phif = 0.0;
     if (k >= 1) {
         const double up = uoth[n];
         const double tk = __dmul_rn((double)k, d.dt);
         const double d2 = __dadd_rn(__dsub_rn(un, __dmul_rn(2.0, uc)), up);
         const double phi = __dmul_rn(__dmul_rn(tk, d2), __dmul_rn(d.inv_dt, d.inv_dt));
         absphi = fabs(phi);
+        if (d.S_par) *phif = __dmul_rn(phi, (double)d.f[n]);
         const int m = d.band_of_k[k];
         const int mp = (k >= 2) ? d.band_of_k[k - 1] : -1;
         double acc = 0.0;

@@ -115,7 +115,7 @@ __device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gs
     const int nbx = (W + kEpBlock - 1) / kEpBlock;
     const int i = lb / nbx;
     const int j = (lb % nbx) * kEpBlock + threadIdx.x;
-    double absphi = 0.0;
+    double absphi = 0.0, phif = 0.0;
     if (j < W) {
         // the copy of p written by the step's last launch
         const int cp = p_copy(k + 1, launches_per_step(d->n_inner, depth), 0);
@@ -126,13 +126,15 @@ __device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gs
             div_at(i, j, H, W, PStore<P>::load(p1[o]), i > 0 ? PStore<P>::load(p1[o - pitch]) : 0.0f,
                    PStore<P>::load(p2[o]), j > 0 ? PStore<P>::load(p2[o - 1]) : 0.0f);
         float gl_next;
-        absphi = epilogue_pixel(*d, k, (size_t)i * W + j, divp, &gl_next);
+        absphi = epilogue_pixel(*d, k, (size_t)i * W + j, divp, &gl_next, &phif);
         d->gl[o] = gl_next;
     }
     if (k < 1) return;  // no phi at step 0
     const double bsum = block_sum(absphi, s_red);
+    const double psum = d->S_par ? block_sum(phif, s_red) : 0.0;  // uniform per image
     if (threadIdx.x == 0) {
         d->partials[lb] = bsum;
+        if (d->S_par) d->partials_par[lb] = psum;
         __threadfence();
         const unsigned prev = atomicAdd(d->counter, 1u);
         s_last = (prev == (unsigned)d->ep_blocks - 1u);
@@ -145,8 +147,16 @@ __device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gs
     const volatile double *parts = d->partials;
     for (int q = threadIdx.x; q < d->ep_blocks; q += kEpBlock) t += parts[q];
     const double tot = block_sum(t, s_red);
+    double ptot = 0.0;
+    if (d->S_par) {
+        double tp = 0.0;
+        const volatile double *pp = d->partials_par;
+        for (int q = threadIdx.x; q < d->ep_blocks; q += kEpBlock) tp += pp[q];
+        ptot = block_sum(tp, s_red);
+    }
     if (threadIdx.x == 0) {
         d->S[k - 1] = tot;
+        if (d->S_par) d->S_par[k - 1] = ptot;
         *d->counter = 0u;
     }
 }

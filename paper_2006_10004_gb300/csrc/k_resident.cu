@@ -14,6 +14,52 @@
 
 namespace tvspec {
 
+// The sum of vals (H x W) exactly as the multi-block epilogue forms S: one 256-wide block per
+// image row (thread t holds column t, zero past W, shuffle tree per warp, then the first warp
+// over the 8 warp sums), then the row sums in one such block. Valid in thread 0; every thread
+// of the CTA must call it.
+template <int RW>
+__device__ __forceinline__ double resident_sum(const double *vals, int H, int W,
+                                               double (*s_red)[8], double *s_part) {
+    constexpr int NG = RW / 8;  // groups of 256 threads
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int g = threadIdx.x >> 8;
+    const int t = threadIdx.x & 255;
+    const int wg = t >> 5;
+    for (int i0 = 0; i0 < H; i0 += NG) {
+        const int i = i0 + g;
+        double v = (i < H && t < W) ? vals[(size_t)i * W + t] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+        if (lane == 0) s_red[g][wg] = v;
+        __syncthreads();
+        if (wg == 0) {
+            double x = lane < 8 ? s_red[g][lane] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULL, x, off);
+            if (lane == 0 && i < H) s_part[i] = x;
+        }
+        __syncthreads();
+    }
+    if (g == 0) {
+        double v = 0.0;
+        if (t < H) v += s_part[t];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
+        if (lane == 0) s_red[0][wg] = v;
+    }
+    __syncthreads();
+    double x = 0.0;
+    if (threadIdx.x < 32) {
+        x = lane < 8 ? s_red[0][lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULL, x, off);
+    }
+    __syncthreads();
+    return x;
+}
+
 template <int V, int R, int RW, int MINB, bool FAST>
 __global__ void __launch_bounds__(32 * RW, MINB)
     k_resident(const ImgDesc *__restrict__ descs, const int *__restrict__ idx, float tau,
@@ -23,15 +69,15 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     constexpr int TW = 32 * V;
     constexpr int TH = RW * R;
     constexpr int NG = RW / 8;  // groups of 256 threads
-    constexpr unsigned FULL = 0xffffffffu;
     __shared__ __align__(16) float s_p1b[RW][TW];
     __shared__ __align__(16) float s_wt[RW][TW];
     __shared__ double s_red[NG][8];
     __shared__ double s_part[TH];
-    extern __shared__ double s_phi[];  // H * W values of |phi_k|
+    extern __shared__ double s_phi[];  // H * W values of |phi_k| [, H * W values of phi_k f]
 
     const ImgDesc &d = descs[idx[blockIdx.x]];
     const int H = d.H, W = d.W, pitch = d.pitch;
+    double *s_phif = s_phi + (size_t)H * W;  // used only when the launch has room for it
     const int lane = threadIdx.x & 31;
     const int wy = threadIdx.x >> 5;
     const int cx = lane * V;
@@ -135,8 +181,10 @@ __global__ void __launch_bounds__(32 * RW, MINB)
                         const float pv2 = h == 0 ? p2[r][j].x : p2[r][j].y;
                         const double divp = div_at(y, c, H, W, pv1, y > 0 ? gp1[o - pitch] : 0.0f,
                                                    pv2, c > 0 ? gp2[o - 1] : 0.0f);
-                        const double a = epilogue_pixel(d, k, (size_t)y * W + c, divp, &g2[h]);
+                        double pf;
+                        const double a = epilogue_pixel(d, k, (size_t)y * W + c, divp, &g2[h], &pf);
                         s_phi[(size_t)y * W + c] = a;
+                        if (d.S_par) s_phif[(size_t)y * W + c] = pf;
                     }
                 }
                 gl[r][j] = make_float2(g2[0], g2[1]);
@@ -144,39 +192,11 @@ __global__ void __launch_bounds__(32 * RW, MINB)
         }
         __syncthreads();
         if (k >= 1) {
-            // S(t_k) exactly as the multi-block epilogue sums it: one 256-wide block per row
-            // (thread t holds column t, zero past W), then the row sums in one block
-            const int g = threadIdx.x >> 8;
-            const int t = threadIdx.x & 255;
-            const int wg = t >> 5;
-            for (int i0 = 0; i0 < H; i0 += NG) {
-                const int i = i0 + g;
-                double v = (i < H && t < W) ? s_phi[(size_t)i * W + t] : 0.0;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
-                if (lane == 0) s_red[g][wg] = v;
-                __syncthreads();
-                if (wg == 0) {
-                    double x = lane < 8 ? s_red[g][lane] : 0.0;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULL, x, off);
-                    if (lane == 0 && i < H) s_part[i] = x;
-                }
-                __syncthreads();
-            }
-            if (g == 0) {
-                double v = 0.0;
-                if (t < H) v += s_part[t];
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
-                if (lane == 0) s_red[0][wg] = v;
-            }
-            __syncthreads();
-            if (threadIdx.x < 32) {
-                double x = lane < 8 ? s_red[0][lane] : 0.0;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULL, x, off);
-                if (lane == 0) d.S[k - 1] = x;
+            const double tot = resident_sum<RW>(s_phi, H, W, s_red, s_part);
+            if (threadIdx.x == 0) d.S[k - 1] = tot;
+            if (d.S_par) {
+                const double ptot = resident_sum<RW>(s_phif, H, W, s_red, s_part);
+                if (threadIdx.x == 0) d.S_par[k - 1] = ptot;
             }
             __syncthreads();
         }
@@ -231,12 +251,12 @@ int resident_variant_for(int H, int W, int preferred) {
 }
 
 cudaError_t launch_resident(int variant, bool fast, const ImgDesc *descs, const int *idx, int n,
-                            float tau, int warm_start, cudaStream_t st) {
+                            float tau, int warm_start, bool parseval, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (variant < 0 || variant >= kNumResident) return cudaErrorInvalidValue;
     const ResidentVariant &v = kResident[variant];
     const ResidentKernel k = fast ? v.fast : v.ieee;
-    const size_t smem = (size_t)(32 * v.V) * (v.RW * v.R) * sizeof(double);
+    const size_t smem = (size_t)(32 * v.V) * (v.RW * v.R) * sizeof(double) * (parseval ? 2 : 1);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<n, 32 * v.RW, smem, st>>>(descs, idx, tau, warm_start);

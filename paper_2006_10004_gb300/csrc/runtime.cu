@@ -103,11 +103,11 @@ tvspec_status make_job(const tvspec_request &req, Job *out) {
 // ---------------------------------------------------------------------------------------------
 struct SlotLayout {
     size_t band, fH, fres, f, p1, p2, q1, q2, gl, acc, facc, filt, bands, partials, ctr, ua, ub,
-        res, S, tr, zero_begin, zero_end, total;
+        res, S, tr, spar, ppar, zero_begin, zero_end, total;
 };
 
 static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naive, bool trace,
-                             int nf = 0) {
+                             int nf = 0, bool par = false) {
     SlotLayout L{};
     const size_t N = (size_t)H * W;
     const int pitch = pitch_for(W);
@@ -140,13 +140,15 @@ static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naiv
     L.res = take(N * 4);
     L.S = take((size_t)std::max(K - 1, 1) * 8);
     L.tr = trace ? take((size_t)(K + 1) * N * 8) : 0;
+    L.spar = par ? take((size_t)std::max(K - 1, 1) * 8) : 0;
+    L.ppar = par ? take((size_t)ep_blocks_for(H, W) * 8) : 0;
     L.total = off;
     return L;
 }
 
 size_t slot_bytes_for(const Job &j, int storage, bool naive) {
     return layout_for(j.r.H, j.r.W, j.r.K, j.r.n_edges - 1, storage, naive, j.r.u_trace != nullptr,
-                      j.r.n_filters)
+                      j.r.n_filters, j.r.S_parseval != nullptr)
         .total;
 }
 
@@ -155,7 +157,8 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
     const tvspec_request &r = j.r;
     const bool trace = r.u_trace != nullptr;
     const int nb = r.n_edges - 1;
-    const SlotLayout L = layout_for(r.H, r.W, r.K, nb, storage, naive, trace, r.n_filters);
+    const bool par = r.S_parseval != nullptr;
+    const SlotLayout L = layout_for(r.H, r.W, r.K, nb, storage, naive, trace, r.n_filters, par);
     char *base = nullptr;
     cudaError_t e = async_alloc ? cudaMallocAsync((void **)&base, L.total, st)
                                 : cudaMalloc((void **)&base, L.total);
@@ -201,6 +204,8 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
     x.filt_res = (double *)(base + L.fres);
     x.facc = (double *)(base + L.facc);
     x.filtered = (float *)(base + L.filt);
+    x.S_par = par ? (double *)(base + L.spar) : nullptr;
+    x.partials_par = par ? (double *)(base + L.ppar) : nullptr;
     x.ep_blocks = ep_blocks_for(r.H, r.W);
     x.p_bytes = (size_t)r.H * x.pitch * storage_bytes(storage);
     e = cudaMemcpyAsync(x.band_of_k, j.band_of_k.data(), r.K, cudaMemcpyHostToDevice, st);
@@ -248,6 +253,8 @@ ImgDesc slot_desc(const Slot &s, int s0) {
     d.filt_res = s.filt_res;
     d.facc = s.facc;
     d.filtered = s.filtered;
+    d.S_par = s.S_par;
+    d.partials_par = s.partials_par;
     d.H = s.H;
     d.W = s.W;
     d.pitch = s.pitch;
@@ -530,9 +537,11 @@ static tvspec_status enqueue_decomposition(tvspec_plan *plan, CacheEntry &E, cud
     // resident images: their whole decomposition, one launch per variant
     int off = 0;
     for (auto &g : E.res_groups) {
+        bool par = false;
+        for (int i = 0; i < g.second; ++i) par |= E.slots[E.n_tiled + off + i].S_par != nullptr;
         cudaError_t e = launch_resident(g.first, plan->cfg.fast_math != 0, E.ls.d_descs,
                                         E.d_res_idx + off, g.second, plan->cfg.tau,
-                                        plan->cfg.warm_start, st);
+                                        plan->cfg.warm_start, par, st);
         if (e != cudaSuccess) return fail_cuda(e, "resident kernel launch");
         ++*nk;
         off += g.second;
@@ -575,7 +584,7 @@ static std::string job_key(const tvspec_config &c, const std::vector<Job> &jobs)
         k << ';' << j.r.H << 'x' << j.r.W << ',' << j.r.K << ',' << j.r.n_inner << ',' << j.r.dt
           << ',' << (j.r.u_trace ? 1 : 0);
         for (double e : j.edges) k << ',' << e;
-        k << ",f" << j.r.n_filters;
+        k << ",f" << j.r.n_filters << ",p" << (j.r.S_parseval ? 1 : 0);
         for (double v : j.filt_H) k << ',' << v;
         for (double v : j.filt_res) k << ',' << v;
     }
@@ -798,7 +807,8 @@ static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStr
                                 {sl.residual, r.residual, N * 4},
                                 {sl.S, r.S, (size_t)(r.K - 1) * 8},
                                 {sl.utrace, r.u_trace, r.u_trace ? (size_t)(r.K + 1) * N * 8 : 0},
-                                {sl.filtered, r.filtered, (size_t)r.n_filters * N * 4}};
+                                {sl.filtered, r.filtered, (size_t)r.n_filters * N * 4},
+                                {sl.S_par, r.S_parseval, r.S_parseval ? (size_t)(r.K - 1) * 8 : 0}};
         for (const CopyItem &c : out) {
             if (c.bytes == 0) continue;
             if (listed) cout.push_back(c);

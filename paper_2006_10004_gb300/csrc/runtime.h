@@ -57,6 +57,7 @@ struct Slot {
     int n_filters = 0;
     double *filt_H = nullptr, *filt_res = nullptr, *facc = nullptr;
     float *filtered = nullptr;
+    double *S_par = nullptr, *partials_par = nullptr;  // Parseval-type spectrum, if requested
     int ep_blocks = 0;
     size_t p_bytes = 0;  // bytes of one pitched p array (one component, one copy)
 };

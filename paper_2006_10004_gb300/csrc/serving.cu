@@ -115,6 +115,8 @@ static tvspec_status copy_out(cudaStream_t cst, ServeReq &r) {
         TV_CK(cudaMemcpyAsync(q.u_trace, r.slot.utrace, (size_t)(q.K + 1) * N * 8, cudaMemcpyDeviceToHost, cst));
     if (q.n_filters > 0)
         TV_CK(cudaMemcpyAsync(q.filtered, r.slot.filtered, (size_t)q.n_filters * N * 4, cudaMemcpyDeviceToHost, cst));
+    if (q.S_parseval)
+        TV_CK(cudaMemcpyAsync(q.S_parseval, r.slot.S_par, (size_t)(q.K - 1) * 8, cudaMemcpyDeviceToHost, cst));
     unsigned status = 0;
     TV_CK(cudaMemcpyAsync(&status, r.slot.status, sizeof(unsigned), cudaMemcpyDeviceToHost, cst));
     TV_CK(cudaStreamSynchronize(cst));

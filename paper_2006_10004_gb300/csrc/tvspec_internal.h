@@ -41,6 +41,8 @@ struct ImgDesc {
     const double *filt_res; // n_filters residual weights
     double *facc;           // n_filters x H x W running filter sums (compact)
     float *filtered;        // n_filters x H x W output (compact), device
+    double *S_par;          // K-1 values <phi_k, f>, or nullptr (not requested)
+    double *partials_par;   // per-epilogue-block partial sums of phi_k f
     int H, W, pitch;
     int K, n_inner;
     int s0;                 // global step at which this image's step 0 runs
@@ -123,8 +125,9 @@ cudaError_t launch_step_coop(int shape, bool fast, const ImgDesc &d, int gstep, 
 int resident_variant_for(int H, int W, int preferred = -1);
 int resident_variant_count();
 bool resident_variant_info(int i, int *max_h, int *max_w, int *threads, int *minb);
+// parseval: some image of the launch wants the Parseval-type spectrum (twice the shared memory).
 cudaError_t launch_resident(int variant, bool fast, const ImgDesc *descs, const int *idx, int n,
-                            float tau, int warm_start, cudaStream_t st);
+                            float tau, int warm_start, bool parseval, cudaStream_t st);
 
 // One iteration per launch over one image (reference GPU kernel): p_in -> p_out.
 cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,
