@@ -13,6 +13,9 @@ Functions and the passages they follow:
   (the discrete form of J_TV, Eq. TV; Chambolle 2004 as cited in Sec. 4.3).
 * ``chambolle``      -- fixed-iteration Chambolle projection for one ROF step (Eq. ROF).
 * ``rof_gap``        -- duality gap of a ROF step (diagnostic).
+* ``fgp`` / ``pdhg`` / ``rof_gap_pair`` -- other inner solvers of the ROF step (Beck-Teboulle's
+  fast gradient projection on the same dual; Chambolle-Pock's primal-dual method, the family
+  of the GPU toolbox Sec. 4.3 times) and the gap of a primal-dual pair.
 * ``decompose``      -- TV flow by implicit Euler (Eq. TVflow, Eq. ROF), phi (Eq. TVtrafo),
   S(t) (Sec. 2.1), bands (Eq. spectral_bands), residual (Eq. finite_inverse_trafo) and
   filtered images (Eq. filteredTVtrafo substituted into Eq. finite_inverse_trafo).
@@ -84,6 +87,13 @@ def _lib():
             h.orc_crop.restype = ctypes.c_int
             h.orc_standardize.argtypes = [_dp, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, _dp, _dp]
             h.orc_standardize.restype = ctypes.c_int
+            h.orc_fgp.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
+            h.orc_fgp.restype = ctypes.c_int
+            h.orc_pdhg.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+            h.orc_pdhg.restype = ctypes.c_int
+            h.orc_rof_gap_pair.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+            h.orc_rof_gap_pair.restype = ctypes.c_double
             h.orc_max_threads.argtypes = []
             h.orc_max_threads.restype = ctypes.c_int
             _handle = h
@@ -138,6 +148,40 @@ def chambolle(g, lam: float, n_iter: int, tau: float = 0.125, p1=None, p2=None):
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
     return u, p1, p2
+
+
+def fgp(g, lam: float, n_iter: int, p1=None, p2=None):
+    """``n_iter`` fast-gradient-projection iterations on the ROF dual; returns (u, p1, p2)."""
+    g = _f64(g)
+    H, W = g.shape
+    p1 = np.zeros_like(g) if p1 is None else _f64(p1).copy()
+    p2 = np.zeros_like(g) if p2 is None else _f64(p2).copy()
+    u = np.empty_like(g)
+    if _lib().orc_fgp(_ptr(g), H, W, float(lam), int(n_iter), _ptr(p1), _ptr(p2), _ptr(u)) != 0:
+        raise MemoryError("oracle: allocation failed")
+    return u, p1, p2
+
+
+def pdhg(g, lam: float, n_iter: int, tau: float = 0.25, sigma: float = 0.5, gamma: float = 0.7,
+         u=None, p1=None, p2=None):
+    """``n_iter`` primal-dual iterations of the ROF step (gamma > 0: accelerated); returns
+    (u, p1, p2) with p the dual in Chambolle's scaling (|p| <= 1)."""
+    g = _f64(g)
+    H, W = g.shape
+    u = g.copy() if u is None else _f64(u).copy()
+    p1 = np.zeros_like(g) if p1 is None else _f64(p1).copy()
+    p2 = np.zeros_like(g) if p2 is None else _f64(p2).copy()
+    if _lib().orc_pdhg(_ptr(g), H, W, float(lam), int(n_iter), float(tau), float(sigma), float(gamma),
+                       _ptr(u), _ptr(p1), _ptr(p2)) != 0:
+        raise MemoryError("oracle: allocation failed")
+    return u, p1, p2
+
+
+def rof_gap_pair(g, lam: float, u, p1, p2) -> float:
+    """P(u) - D(p) of the ROF step for a primal-dual pair (|p| <= 1)."""
+    g, u, p1, p2 = _f64(g), _f64(u), _f64(p1), _f64(p2)
+    H, W = g.shape
+    return float(_lib().orc_rof_gap_pair(_ptr(g), H, W, float(lam), _ptr(u), _ptr(p1), _ptr(p2)))
 
 
 def rof_gap(g, lam: float, p1, p2) -> float:

@@ -377,3 +377,155 @@ int orc_standardize(const double *x, int n_img, size_t npx, int mode, double *me
     }
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Other inner solvers of the ROF step (Eq. ROF), for comparison with Chambolle's projection:
+ * the fast gradient projection on the same dual problem and the primal-dual hybrid gradient
+ * method (the family of the GPU toolbox the paper times in Sec. 4.3), and the duality gap of
+ * a primal-dual pair, by which their accuracy is compared.
+ * -------------------------------------------------------------------------------------------*/
+
+/* p <- p / max(1, |p|) pointwise (projection onto the unit ball of the isotropic norm). */
+static void orc_project_unit(double *p1, double *p2, size_t N)
+{
+#pragma omp parallel for schedule(static) if (N >= OMP_MIN_PIXELS)
+    for (long long n = 0; n < (long long)N; ++n) {
+        double norm = sqrt(p1[n] * p1[n] + p2[n] * p2[n]);
+        if (norm > 1.0) {
+            p1[n] = p1[n] / norm;
+            p2[n] = p2[n] / norm;
+        }
+    }
+}
+
+/*
+ * n_iter iterations of the fast gradient projection (Beck and Teboulle 2009, FGP) on
+ * Chambolle's dual of the ROF step:  min over |p| <= 1 of |g - lambda div p|^2.
+ * From r = p_prev = p (the given start) and t = 1, one iteration is
+ *   p_new = Pi( r + (1/8) grad(div r - g / lambda) )    (gradient step 1/8 = 1/|div|^2)
+ *   t_new = (1 + sqrt(1 + 4 t^2)) / 2
+ *   r     = p_new + ((t - 1) / t_new) (p_new - p_prev),  p_prev = p_new,  t = t_new
+ * and u = g - lambda div p at the end. p1, p2: start on entry, final p on exit.
+ */
+int orc_fgp(const double *g, int H, int W, double lambda, int n_iter, double *p1, double *p2,
+            double *u_out)
+{
+    size_t N = (size_t)H * (size_t)W;
+    double *r1 = (double *)malloc(N * sizeof(double));
+    double *r2 = (double *)malloc(N * sizeof(double));
+    double *d = (double *)malloc(N * sizeof(double));
+    double *w = (double *)malloc(N * sizeof(double));
+    double *G1 = (double *)malloc(N * sizeof(double));
+    double *G2 = (double *)malloc(N * sizeof(double));
+    double *n1 = (double *)malloc(N * sizeof(double));
+    double *n2 = (double *)malloc(N * sizeof(double));
+    if (!r1 || !r2 || !d || !w || !G1 || !G2 || !n1 || !n2) {
+        free(r1); free(r2); free(d); free(w); free(G1); free(G2); free(n1); free(n2);
+        return -1;
+    }
+    memcpy(r1, p1, N * sizeof(double));
+    memcpy(r2, p2, N * sizeof(double));
+    double t = 1.0;
+    for (int it = 0; it < n_iter; ++it) {
+        orc_div(r1, r2, H, W, d);
+        for (size_t n = 0; n < N; ++n)
+            w[n] = d[n] - g[n] / lambda;
+        orc_grad(w, H, W, G1, G2);
+        for (size_t n = 0; n < N; ++n) {
+            n1[n] = r1[n] + G1[n] / 8.0;
+            n2[n] = r2[n] + G2[n] / 8.0;
+        }
+        orc_project_unit(n1, n2, N);
+        double t_new = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+        double beta = (t - 1.0) / t_new;
+        for (size_t n = 0; n < N; ++n) {
+            r1[n] = n1[n] + beta * (n1[n] - p1[n]);
+            r2[n] = n2[n] + beta * (n2[n] - p2[n]);
+            p1[n] = n1[n];
+            p2[n] = n2[n];
+        }
+        t = t_new;
+    }
+    orc_div(p1, p2, H, W, d);
+    for (size_t n = 0; n < N; ++n)
+        u_out[n] = g[n] - lambda * d[n];
+    free(r1); free(r2); free(d); free(w); free(G1); free(G2); free(n1); free(n2);
+    return 0;
+}
+
+/*
+ * n_iter iterations of the primal-dual hybrid gradient method (Chambolle and Pock 2011; with
+ * gamma > 0 their accelerated variant for a uniformly convex data term) on the saddle-point
+ * form of the ROF step,  min_u max_{|y| <= lambda} <grad u, y> + 1/2 |u - g|^2,
+ * written with the dual variable p = -y / lambda (|p| <= 1, the same p as Chambolle's, so
+ * that u(p) = g - lambda div p). From (u, ubar = u, p) and steps (tau, sigma):
+ *   p     = Pi( p - (sigma / lambda) grad ubar )
+ *   u_new = (u - tau lambda div p + tau g) / (1 + tau)
+ *   theta = 1 / sqrt(1 + 2 gamma tau)   (theta = 1 when gamma = 0)
+ *   ubar  = u_new + theta (u_new - u),  u = u_new,  tau = theta tau,  sigma = sigma / theta
+ * Convergence needs tau sigma |grad|^2 <= 1, |grad|^2 <= 8. u, p1, p2: start on entry, final
+ * iterates on exit.
+ */
+int orc_pdhg(const double *g, int H, int W, double lambda, int n_iter, double tau, double sigma,
+             double gamma, double *u, double *p1, double *p2)
+{
+    size_t N = (size_t)H * (size_t)W;
+    double *ub = (double *)malloc(N * sizeof(double));
+    double *d = (double *)malloc(N * sizeof(double));
+    double *G1 = (double *)malloc(N * sizeof(double));
+    double *G2 = (double *)malloc(N * sizeof(double));
+    if (!ub || !d || !G1 || !G2) {
+        free(ub); free(d); free(G1); free(G2);
+        return -1;
+    }
+    memcpy(ub, u, N * sizeof(double));
+    for (int it = 0; it < n_iter; ++it) {
+        orc_grad(ub, H, W, G1, G2);
+        for (size_t n = 0; n < N; ++n) {
+            p1[n] = p1[n] - (sigma / lambda) * G1[n];
+            p2[n] = p2[n] - (sigma / lambda) * G2[n];
+        }
+        orc_project_unit(p1, p2, N);
+        orc_div(p1, p2, H, W, d);
+        double theta = gamma > 0.0 ? 1.0 / sqrt(1.0 + 2.0 * gamma * tau) : 1.0;
+        for (size_t n = 0; n < N; ++n) {
+            double un = (u[n] - tau * lambda * d[n] + tau * g[n]) / (1.0 + tau);
+            ub[n] = un + theta * (un - u[n]);
+            u[n] = un;
+        }
+        tau = theta * tau;
+        sigma = sigma / theta;
+    }
+    free(ub); free(d); free(G1); free(G2);
+    return 0;
+}
+
+/*
+ * Duality gap of a primal-dual pair (u, p) of the ROF step, |p| <= 1:
+ *   P(u) - D(p) = 1/2 |u - g|^2 + lambda sum |grad u|  -  (1/2 |g|^2 - 1/2 |g - lambda div p|^2)
+ * >= P(u) - P(u*) >= 1/2 |u - u*|^2.
+ */
+double orc_rof_gap_pair(const double *g, int H, int W, double lambda, const double *u,
+                        const double *p1, const double *p2)
+{
+    size_t N = (size_t)H * (size_t)W;
+    double *d = (double *)malloc(N * sizeof(double));
+    double *G1 = (double *)malloc(N * sizeof(double));
+    double *G2 = (double *)malloc(N * sizeof(double));
+    if (!d || !G1 || !G2) {
+        free(d); free(G1); free(G2);
+        return NAN;
+    }
+    orc_div(p1, p2, H, W, d);
+    orc_grad(u, H, W, G1, G2);
+    double fid = 0.0, tv = 0.0, gg = 0.0, rr = 0.0;
+    for (size_t n = 0; n < N; ++n) {
+        double r = g[n] - lambda * d[n];
+        fid += 0.5 * (u[n] - g[n]) * (u[n] - g[n]);
+        tv += sqrt(G1[n] * G1[n] + G2[n] * G2[n]);
+        gg += 0.5 * g[n] * g[n];
+        rr += 0.5 * r * r;
+    }
+    free(d); free(G1); free(G2);
+    return (fid + lambda * tv) - (gg - rr);
+}
