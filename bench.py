@@ -352,6 +352,7 @@ def run_gb300(args):
         result["m1024"] = {"workload": syn.m1024.__doc__.strip().splitlines()[0], "decomps_per_s": 1000.0 / ms,
                            "ms_per_decomp": ms, "Mpx_iter_per_s": m.px_iters / ms / 1e3}
         result["filter_bank_config1"] = measure_filters(tv, torch, plan, job, f_dev, stream, flush)
+        result["inner_solvers"] = measure_solvers(tv, torch, plan, job, stream)
         result["batched_config2"] = measure_batched(tv, torch, local, 2, 1)
         result["training_crops"] = measure_crops(tv, torch, local)
         sv = measure_serving(tv, local, [float(args.serve_rate)], args.serve_requests)[0]
@@ -402,6 +403,32 @@ def measure_filters(tv, torch, plan, job, f_dev, stream, flush, n_filters: int =
     return {"filters": n_filters, "ms_with_filters": filt, "ms_without": plain,
             "overhead_frac": filt / plain - 1.0,
             "Mpx_iter_per_s_with_filters": job.px_iters / filt / 1e3}
+
+
+def measure_solvers(tv, torch, plan, job, stream, targets=(1e-4, 1e-5), check_every: int = 25):
+    """Inner solvers of one ROF step (the first step of the bench image, lambda = dt): for each
+    per-pixel duality-gap target, the iterations and wall time (gap checks included) each
+    solver needs, and each solver's device time per iteration."""
+    g = torch.from_numpy(job.f).to(stream.device)
+    N = job.f.size
+    out = {"image": f"{job.f.shape[0]}x{job.f.shape[1]}", "lambda": job.dt, "check_every": check_every}
+    for name in ("chambolle", "fgp", "pdhg"):
+        plan.rof_solve(g, job.dt, name, max_iter=100, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = plan.rof_solve(g, job.dt, name, max_iter=1000, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        row = {"us_per_iteration": e0.elapsed_time(e1) * 1e3 / 1000, "gap_at_1000": r["gap"] / N}
+        for tgt in targets:
+            t0 = time.perf_counter()
+            r = plan.rof_solve(g, job.dt, name, max_iter=50000, gap_tol=tgt * N, check_every=check_every,
+                               stream=stream)
+            row[f"to_{tgt:g}"] = {"iterations": r["iterations"], "ms": 1e3 * (time.perf_counter() - t0),
+                                 "gap_per_px": r["gap"] / N}
+        out[name] = row
+    return out
 
 
 def measure_batched(tv, torch, local, steps: int, warmup: int, with_clocks=None):

@@ -265,6 +265,42 @@ tvspec_status tvspec_rof_step(tvspec_plan *plan, const float *g, int H, int W, d
 tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float *p1, float *p2,
                                        int H, int W, int pitch, int n_iter, void *stream);
 
+/* Inner solvers of one ROF step (Eq. ROF), for comparing accuracy per iteration and time:
+ *   TVSPEC_SOLVER_CHAMBOLLE  Chambolle's projection (the decomposition's solver; the tiled,
+ *                            temporally blocked kernel)
+ *   TVSPEC_SOLVER_FGP        Beck and Teboulle's fast gradient projection on the same dual
+ *                            (step 1/8, Nesterov momentum)
+ *   TVSPEC_SOLVER_PDHG       Chambolle and Pock's primal-dual hybrid gradient method (the
+ *                            family of the GPU toolbox timed in Sec. 4.3); accelerated when
+ *                            pdhg_gamma > 0 (steps tau_n, sigma_n, theta_n updated per
+ *                            iteration), basic with theta = 1 when pdhg_gamma == 0. */
+enum { TVSPEC_SOLVER_CHAMBOLLE = 0, TVSPEC_SOLVER_FGP = 1, TVSPEC_SOLVER_PDHG = 2 };
+
+typedef struct tvspec_rof_request {
+    const float *g;         /* in: H*W image (mem_kind memory) */
+    int H, W;
+    double lambda;          /* ROF weight (the flow's dt), > 0 */
+    int solver;             /* TVSPEC_SOLVER_* */
+    int max_iter;           /* 0..1e7 */
+    double gap_tol;         /* > 0: stop at the first check with duality gap <= gap_tol (sum
+                               over pixels); <= 0: run max_iter iterations */
+    int check_every;        /* iterations between gap evaluations, >= 1 */
+    float pdhg_tau, pdhg_sigma, pdhg_gamma;  /* PDHG steps, tau sigma <= 1/8, gamma >= 0 */
+    const float *p1_in, *p2_in;  /* optional (NULL = 0): starting dual field, H*W each, in
+                                    Chambolle's scaling |p| <= 1 */
+    float *u;               /* out: H*W primal iterate (dual methods: g - lambda div p) */
+    float *p1, *p2;         /* out, optional (NULL): final dual field, H*W each */
+    int mem_kind;           /* g, p*_in, u, p1, p2 */
+    int iterations;         /* out: iterations run */
+    double gap;             /* out: duality gap P(u) - D(p) of the returned pair, float64 */
+} tvspec_rof_request;
+
+/* Runs one ROF step with the chosen solver. The duality gap of the pair (u, p) is
+ * 1/2|u-g|^2 + lambda sum|grad u| - (1/2|g|^2 - 1/2|g - lambda div p|^2), reduced in float64
+ * in a fixed order; it bounds 1/2|u - u*|^2. Checking it costs one host synchronisation per
+ * check. Synchronous. Errors: EINVAL, ENOMEM, ECUDA, ENOTSUP (p_storage other than fp32). */
+tvspec_status tvspec_rof_solve(tvspec_plan *plan, tvspec_rof_request *req, void *stream);
+
 /* The decomposition without any device allocation. No counterpart in the paper: this entry
  * exists for callers that cannot call cudaMalloc/cudaFree where they run (a thread working
  * while another captures a CUDA graph in global mode, real-time loops that cannot take the

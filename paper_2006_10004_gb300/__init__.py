@@ -23,6 +23,8 @@ __all__ = ["Plan", "Config", "TvSpecError", "load", "build", "STATUS"]
 STATUS = {0: "TVSPEC_OK", 1: "TVSPEC_EINVAL", 2: "TVSPEC_ENOMEM", 3: "TVSPEC_ECUDA",
           4: "TVSPEC_ETIMEOUT", 5: "TVSPEC_ENOTREADY", 6: "TVSPEC_ECANCELLED", 7: "TVSPEC_ENOTSUP"}
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTREADY, ECANCELLED, ENOTSUP = range(8)
+SOLVER_CHAMBOLLE, SOLVER_FGP, SOLVER_PDHG = range(3)
+SOLVERS = {"chambolle": SOLVER_CHAMBOLLE, "fgp": SOLVER_FGP, "pdhg": SOLVER_PDHG}
 P_FP32, P_FP16, P_BF16 = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_TILED = 0, 1, 2
@@ -72,6 +74,15 @@ class TrainingRequest(ctypes.Structure):
                 ("stats", ctypes.c_void_p), ("mem_kind", ctypes.c_int)]
 
 
+class RofRequest(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("lam", ctypes.c_double),
+                ("solver", ctypes.c_int), ("max_iter", ctypes.c_int), ("gap_tol", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("pdhg_tau", ctypes.c_float), ("pdhg_sigma", ctypes.c_float),
+                ("pdhg_gamma", ctypes.c_float), ("p1_in", ctypes.c_void_p), ("p2_in", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("p1", ctypes.c_void_p), ("p2", ctypes.c_void_p),
+                ("mem_kind", ctypes.c_int), ("iterations", ctypes.c_int), ("gap", ctypes.c_double)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
                 ("graphs_built", ctypes.c_uint64), ("decompositions", ctypes.c_uint64),
@@ -95,6 +106,7 @@ _SIGS = {
     "tvspec_decompose_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_void_p]),
     "tvspec_resident_variant_count": (ctypes.c_int, []),
     "tvspec_resident_variant_info": (ctypes.c_int, [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4),
+    "tvspec_rof_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RofRequest), ctypes.c_void_p]),
     "tvspec_training_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TrainingRequest), ctypes.c_void_p]),
     "tvspec_decompose_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Request),
                                               ctypes.c_void_p]),
@@ -455,6 +467,37 @@ class Plan:
         _check(self._lib.tvspec_rof_step(self._h, ptr(g), H, W, float(lam), int(n_iter), ptr(p1), ptr(p2),
                                          ptr(u), kind, st), "tvspec_rof_step")
         return u, p1, p2
+
+    def rof_solve(self, g, lam: float, solver="chambolle", max_iter: int = 1000, gap_tol: float = 0.0,
+                  check_every: int = 50, p_in=None, tau: float = 0.25, sigma: float = 0.5, gamma: float = 0.7,
+                  stream=None) -> dict:
+        """One ROF step by the chosen solver ("chambolle", "fgp", "pdhg"); stops at the first
+        check with duality gap <= gap_tol (if > 0). Returns u, p1, p2, iterations, gap."""
+        sv = SOLVERS[solver] if isinstance(solver, str) else int(solver)
+        if _is_torch_cuda(g):
+            import torch
+
+            g = g.contiguous().float()
+            u = torch.empty_like(g)
+            p1 = torch.empty_like(g)
+            p2 = torch.empty_like(g)
+            pin = None if p_in is None else (p_in[0].contiguous().float(), p_in[1].contiguous().float())
+            ptr = lambda t: t.data_ptr()
+            kind, st = MEM_DEVICE, _stream_ptr(stream)
+        else:
+            g = np.ascontiguousarray(np.asarray(g, np.float32))
+            u, p1, p2 = np.empty_like(g), np.empty_like(g), np.empty_like(g)
+            pin = None if p_in is None else tuple(np.ascontiguousarray(np.asarray(x, np.float32)) for x in p_in)
+            ptr = lambda a: a.ctypes.data
+            kind, st = MEM_HOST, None
+        H, W = g.shape
+        r = RofRequest(g=ptr(g), H=H, W=W, lam=float(lam), solver=sv, max_iter=int(max_iter),
+                       gap_tol=float(gap_tol), check_every=int(check_every), pdhg_tau=float(tau),
+                       pdhg_sigma=float(sigma), pdhg_gamma=float(gamma),
+                       p1_in=ptr(pin[0]) if pin else None, p2_in=ptr(pin[1]) if pin else None,
+                       u=ptr(u), p1=ptr(p1), p2=ptr(p2), mem_kind=kind)
+        _check(self._lib.tvspec_rof_solve(self._h, ctypes.byref(r), st), "tvspec_rof_solve")
+        return {"u": u, "p1": p1, "p2": p2, "iterations": r.iterations, "gap": r.gap}
 
     def chambolle_iterate(self, gl, p1, p2, H: int, W: int, pitch: int, n_iter: int, stream=None):
         """Dual iterations on pitched CUDA tensors (gl, p1, p2 of H*pitch float32), in place."""

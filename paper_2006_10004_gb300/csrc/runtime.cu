@@ -895,8 +895,7 @@ tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *de
 
 // Runs d.n_inner dual iterations as local step 0 of the image described by d (two copies of
 // p, copy 0 holding the start); *final_copy receives the copy holding the result.
-static tvspec_status run_iterations(tvspec_plan *plan, ImgDesc d, cudaStream_t st,
-                                    int *final_copy) {
+tvspec_status run_iterations(tvspec_plan *plan, ImgDesc d, cudaStream_t st, int *final_copy) {
     Slot *tune_slot = nullptr;
     tvspec_status s = scratch_slot(plan, d.H, d.W, &tune_slot);
     if (s != TVSPEC_OK) return s;

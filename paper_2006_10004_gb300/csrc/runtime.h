@@ -146,6 +146,10 @@ tvspec_status enqueue_copy_list(const std::vector<CopyItem> &items, cudaStream_t
 // Makes `later` wait for the work enqueued on `earlier` so far.
 tvspec_status order_after(cudaStream_t later, cudaStream_t earlier);
 
+// n_inner dual iterations of the tiled kernel on one image's buffers d.p1/p2[0..1], d.gl
+// (plan->mu held); *final_copy receives the copy of p that holds the result.
+tvspec_status run_iterations(tvspec_plan *plan, ImgDesc d, cudaStream_t st, int *final_copy);
+
 // Tile choice for an H x W image, tuned on plan-owned scratch buffers (takes the plan lock).
 tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *depth);
 
