@@ -14,47 +14,62 @@
 
 namespace tvspec {
 
-// The sum of vals (H x W) exactly as the multi-block epilogue forms S: one 256-wide block per
-// image row (thread t holds column t, zero past W, shuffle tree per warp, then the first warp
-// over the 8 warp sums), then the row sums in one such block. Valid in thread 0; every thread
-// of the CTA must call it.
+// Shuffle tree of one warp (lane 0 gets the sum), the order of block_sum's first level.
+__device__ __forceinline__ double warp_tree(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// block_sum's second level for 256 threads: lane j < 8 of warp 0 holds warp j's sum, the other
+// 24 lanes zero, then the shuffle tree. Adding those zeros changes nothing but the sign of a
+// zero, which the explicit (x + 0) + 0 reproduces: the result is
+// ((w0 + w4) + (w2 + w6)) + ((w1 + w5) + (w3 + w7)) with w = (w + 0) + 0.
+__device__ __forceinline__ double eight_tree(const double (&w)[8]) {
+    double z[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) z[c] = __dadd_rn(__dadd_rn(w[c], 0.0), 0.0);
+    return __dadd_rn(__dadd_rn(__dadd_rn(z[0], z[4]), __dadd_rn(z[2], z[6])),
+                     __dadd_rn(__dadd_rn(z[1], z[5]), __dadd_rn(z[3], z[7])));
+}
+
+// The sum of vals (H x W) with exactly the operations of the multi-block epilogue: block_sum
+// over one 256-wide block per image row (thread t holds column t, zero past W), then, in one
+// block, block_sum of (0 + row sum) over the rows. A 256-wide tree is the warp trees of its 8
+// chunks of 32 and eight_tree over them; chunks past the data are all-zero and sum to zero, so
+// one warp per row computes only the chunks that hold data, with no CTA barrier per row.
+// Valid in thread 0; every thread of the CTA must call it (two CTA barriers).
 template <int RW>
-__device__ __forceinline__ double resident_sum(const double *vals, int H, int W,
-                                               double (*s_red)[8], double *s_part) {
-    constexpr int NG = RW / 8;  // groups of 256 threads
-    constexpr unsigned FULL = 0xffffffffu;
+__device__ __forceinline__ double resident_sum(const double *vals, int H, int W, double *s_part) {
     const int lane = threadIdx.x & 31;
-    const int g = threadIdx.x >> 8;
-    const int t = threadIdx.x & 255;
-    const int wg = t >> 5;
-    for (int i0 = 0; i0 < H; i0 += NG) {
-        const int i = i0 + g;
-        double v = (i < H && t < W) ? vals[(size_t)i * W + t] : 0.0;
+    const int warp = threadIdx.x >> 5;
+    const int nch = (W + 31) >> 5;  // <= 8 (W <= 256)
+    for (int i = warp; i < H; i += RW) {
+        double w[8];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
-        if (lane == 0) s_red[g][wg] = v;
-        __syncthreads();
-        if (wg == 0) {
-            double x = lane < 8 ? s_red[g][lane] : 0.0;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULL, x, off);
-            if (lane == 0 && i < H) s_part[i] = x;
+        for (int c = 0; c < 8; ++c) {
+            w[c] = 0.0;
+            if (c < nch) {
+                const int col = 32 * c + lane;
+                w[c] = warp_tree(col < W ? vals[(size_t)i * W + col] : 0.0);
+            }
         }
-        __syncthreads();
-    }
-    if (g == 0) {
-        double v = 0.0;
-        if (t < H) v += s_part[t];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(FULL, v, off);
-        if (lane == 0) s_red[0][wg] = v;
+        if (lane == 0) s_part[i] = eight_tree(w);
     }
     __syncthreads();
     double x = 0.0;
-    if (threadIdx.x < 32) {
-        x = lane < 8 ? s_red[0][lane] : 0.0;
+    if (warp == 0) {
+        const int nr = (H + 31) >> 5;  // <= 8 (H <= 256)
+        double w[8];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(FULL, x, off);
+        for (int c = 0; c < 8; ++c) {
+            w[c] = 0.0;
+            if (c < nr) {
+                const int row = 32 * c + lane;
+                w[c] = warp_tree(row < H ? __dadd_rn(0.0, s_part[row]) : 0.0);
+            }
+        }
+        x = eight_tree(w);
     }
     __syncthreads();
     return x;
@@ -64,14 +79,11 @@ template <int V, int R, int RW, int MINB, bool FAST>
 __global__ void __launch_bounds__(32 * RW, MINB)
     k_resident(const ImgDesc *__restrict__ descs, const int *__restrict__ idx, float tau,
                int warm_start) {
-    static_assert(RW % 8 == 0, "the S reduction works in groups of 8 warps");
     constexpr int VP = V / 2;
     constexpr int TW = 32 * V;
     constexpr int TH = RW * R;
-    constexpr int NG = RW / 8;  // groups of 256 threads
     __shared__ __align__(16) float s_p1b[RW][TW];
     __shared__ __align__(16) float s_wt[RW][TW];
-    __shared__ double s_red[NG][8];
     __shared__ double s_part[TH];
     extern __shared__ double s_phi[];  // H * W values of |phi_k| [, H * W values of phi_k f]
 
@@ -192,10 +204,10 @@ __global__ void __launch_bounds__(32 * RW, MINB)
         }
         __syncthreads();
         if (k >= 1) {
-            const double tot = resident_sum<RW>(s_phi, H, W, s_red, s_part);
+            const double tot = resident_sum<RW>(s_phi, H, W, s_part);
             if (threadIdx.x == 0) d.S[k - 1] = tot;
             if (d.S_par) {
-                const double ptot = resident_sum<RW>(s_phif, H, W, s_red, s_part);
+                const double ptot = resident_sum<RW>(s_phif, H, W, s_part);
                 if (threadIdx.x == 0) d.S_par[k - 1] = ptot;
             }
             __syncthreads();
