@@ -683,6 +683,8 @@ def run_kernel_only(args, tv, torch, local):
     torch.cuda.synchronize()
     depth = max(1, plan.stats()["last_temporal_block"])
     iters = depth * args.launches
+    plan.chambolle_iterate(gl, p1, p2, n, n, pitch, iters, stream=stream)  # same call, untimed
+    torch.cuda.synchronize()
     s0 = plan.stats()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     for (size_t q = threadIdx.x; q < (size_t)d.n_bands * H * W; q += blockDim.x) d.bands[q] = 0.0f;
     __syncthreads();
 
+    const bool exact = H == TH && W == TW;  // uniform over the CTA
     // border masks: the tile is the image, every tile pixel outside it stays zero
     unsigned m1 = 0u, m2 = 0u;
 #pragma unroll
@@ -158,8 +159,12 @@ __global__ void __launch_bounds__(32 * RW, MINB)
             *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
         }
         __syncthreads();
-        tiled_iterate<V, R, RW, FAST, true, true>(p1, p2, gl, d.n_inner, tau, m1, m2, s_p1b,
-                                                  s_wt, lane, wy);
+        if (exact)  // the image fills the tile: masks only on its last row and column
+            tiled_iterate<V, R, RW, FAST, kEdgeExact, true>(p1, p2, gl, d.n_inner, tau, 0u, 0u,
+                                                            s_p1b, s_wt, lane, wy);
+        else
+            tiled_iterate<V, R, RW, FAST, kEdgeMasked, true>(p1, p2, gl, d.n_inner, tau, m1, m2,
+                                                             s_p1b, s_wt, lane, wy);
         // p to global for the divergence's neighbours
 #pragma unroll
         for (int r = 0; r < R; ++r) {

@@ -152,10 +152,10 @@ __global__ void __launch_bounds__(32 * RW, MINB)
         }
         const int n_iter = min(min(depth, TB), d.n_inner - blk * depth);
         if (interior)
-            tiled_iterate<V, R, RW, FAST, false>(p1, p2, gl, n_iter, tau, 0u, 0u, s_p1b, s_wt,
+            tiled_iterate<V, R, RW, FAST, kEdgeNone>(p1, p2, gl, n_iter, tau, 0u, 0u, s_p1b, s_wt,
                                                  lane, wy);
         else
-            tiled_iterate<V, R, RW, FAST, true>(p1, p2, gl, n_iter, tau, m1, m2, s_p1b, s_wt,
+            tiled_iterate<V, R, RW, FAST, kEdgeMasked>(p1, p2, gl, n_iter, tau, m1, m2, s_p1b, s_wt,
                                                 lane, wy);
         // the exact centre into the other copy
         float *o1 = static_cast<float *>(d.p1[src ^ 1]);

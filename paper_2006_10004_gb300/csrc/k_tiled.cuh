@@ -35,11 +35,20 @@ struct alignas(sizeof(float) * V) FPack {
     float v[V];
 };
 
+// Border handling of tiled_iterate:
+//   kEdgeNone   the tile touches no image border (no masks);
+//   kEdgeMasked per-pixel masks m1bits / m2bits (bit r*V + v) for G1 / G2;
+//   kEdgeExact  the tile is exactly the image (rows 0..RW*R-1, columns 0..32V-1): G1 is zero
+//               on the last row and G2 on the last column, nothing else is masked. The same
+//               values as kEdgeMasked with the masks of that image, with a select per row
+//               instead of four per pixel pair.
+constexpr int kEdgeNone = 0, kEdgeMasked = 1, kEdgeExact = 2;
+
 // The iterations of one launch on the registers of one thread. Pixels are processed in
 // horizontal pairs (columns 2q, 2q+1 of the lane) with packed f32x2 arithmetic.
 // ZERO_LEFT: the tile's first column is the image's first column (no halo), so lane 0's left
 // neighbour p2_{i,-1} is 0 rather than a halo value.
-template <int V, int R, int RW, bool FAST, bool EDGE, bool ZERO_LEFT = false>
+template <int V, int R, int RW, bool FAST, int EDGE, bool ZERO_LEFT = false>
 __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
                                               const float2 (&gl)[R][V / 2], int n_iter,
                                               float tau, unsigned m1bits, unsigned m2bits,
@@ -102,12 +111,15 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
                 const float2 wr = make_float2(w[r][j].y, j < VP - 1 ? w[r][j + 1].x : right_last);
                 float2 G1 = sub2(wd, w[r][j]);
                 float2 G2 = sub2(wr, w[r][j]);
-                if (EDGE) {
+                if (EDGE == kEdgeMasked) {
                     const int b0 = r * V + 2 * j;
                     G1.x = ((m1bits >> b0) & 1u) ? G1.x : 0.0f;
                     G1.y = ((m1bits >> (b0 + 1)) & 1u) ? G1.y : 0.0f;
                     G2.x = ((m2bits >> b0) & 1u) ? G2.x : 0.0f;
                     G2.y = ((m2bits >> (b0 + 1)) & 1u) ? G2.y : 0.0f;
+                } else if (EDGE == kEdgeExact) {
+                    if (r == R - 1 && wy == RW - 1) G1 = make_float2(0.0f, 0.0f);  // last row
+                    if (j == VP - 1 && lane == 31) G2.y = 0.0f;                    // last column
                 }
                 tv_update2<FAST>(p1[r][j], p2[r][j], G1, G2, tau);
             }
@@ -195,7 +207,7 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
 
     const bool interior = ys >= 0 && ys + TH <= H - 1 && xs >= 0 && xs + TW <= W - 1;
     if (interior) {
-        tiled_iterate<V, R, RW, FAST, false>(p1, p2, gl, n_iter, tau, 0u, 0u, s_p1b, s_wt, lane,
+        tiled_iterate<V, R, RW, FAST, kEdgeNone>(p1, p2, gl, n_iter, tau, 0u, 0u, s_p1b, s_wt, lane,
                                              wy);
     } else {
         unsigned m1 = 0u, m2 = 0u;
@@ -210,7 +222,7 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
                 if (y >= 0 && y < H && c >= 0 && c < W - 1) m2 |= 1u << (r * V + v);
             }
         }
-        tiled_iterate<V, R, RW, FAST, true>(p1, p2, gl, n_iter, tau, m1, m2, s_p1b, s_wt, lane,
+        tiled_iterate<V, R, RW, FAST, kEdgeMasked>(p1, p2, gl, n_iter, tau, m1, m2, s_p1b, s_wt, lane,
                                             wy);
     }
 
@@ -288,7 +300,11 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     X(20, 2, 8, 8, 8, 4) \
     X(21, 2, 4, 8, 8, 4)         \
     X(22, 2, 8, 8, 8, 1)         \
-    X(23, 4, 4, 8, 8, 1)
+    X(23, 4, 4, 8, 8, 1)         \
+    X(24, 2, 7, 8, 8, 1)         \
+    X(25, 2, 8, 7, 8, 1)         \
+    X(26, 2, 6, 8, 6, 1)         \
+    X(27, 2, 8, 6, 6, 1)
 
 using TiledKernel = void (*)(const TileRef *, const ImgDesc *, int, int, int, float);
 using TiledOneKernel = void (*)(const ImgDesc, int, int, int, int, float);

@@ -127,8 +127,9 @@ struct tvspec_plan {
 namespace tvspec {
 
 // Chooses (shape, depth) for a set of slots (autotuned unless the config fixes them).
+// table_form: time the tile-table kernel even for one image (the serving path always uses it).
 tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, cudaStream_t st,
-                           int *shape, int *depth);
+                           int *shape, int *depth, bool table_form = false);
 
 // Enqueues the device work of one ROF step at global step gstep for the first n_active images
 // of the set (dual iterations + epilogue). Adds the kernels launched to *n_kernels.

@@ -245,7 +245,7 @@ void Server::loop() {
             // that carries most of the served pixels (every shape gives the same bits)
             if (c.tile >= 0) {
                 std::vector<Slot *> none;
-                if (choose_tiles(plan, none, st, &shape, &depth) != TVSPEC_OK) shape = -2;
+                if (choose_tiles(plan, none, st, &shape, &depth, true) != TVSPEC_OK) shape = -2;
             } else if (tune_for_size(plan, 2048, 2048, &shape, &depth) != TVSPEC_OK) {
                 shape = -2;
             }
