@@ -414,36 +414,50 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
             return s;
         }
     }
-    cudaEvent_t e0, e1;
-    TV_CK(cudaEventCreate(&e0));
-    TV_CK(cudaEventCreate(&e1));
+    // Each candidate is timed as the run executes it: a CUDA graph of back-to-back launches
+    // (direct launches would add a launch gap that graph replay does not have, and change the
+    // ranking). Two rounds over all candidates, each candidate's cost the faster of its two:
+    // the first round also brings the GPU to its working clock.
+    constexpr int kReps = 8;
+    std::vector<cudaGraphExec_t> execs(cs.size(), nullptr);
     cudaError_t e = cudaSuccess;
-    // two rounds over all candidates, each candidate's cost the faster of its two: the first
-    // round also brings the GPU to its working clock
+    for (size_t i = 0; i < cs.size() && e == cudaSuccess; ++i) {
+        Cand &x = cs[i];
+        const int nt = x.ls.tile_prefix[x.ls.n];
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        cudaError_t le = cudaSuccess;
+        for (int r = 0; r < kReps && le == cudaSuccess; ++r)
+            le = one ? launch_tiled_one(x.shape, c.p_storage, c.fast_math != 0, x.ls.h_descs[0], 0, 0,
+                                        x.depth, c.tau, st)
+                     : launch_tiled(x.shape, c.p_storage, c.fast_math != 0, x.ls.d_tiles, nt,
+                                    x.ls.d_descs, 0, 0, x.depth, c.tau, st);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (e == cudaSuccess) e = le;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&execs[i], g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
     for (int round = 0; round < 2 && e == cudaSuccess; ++round) {
-        for (Cand &x : cs) {
-            const int nt = x.ls.tile_prefix[x.ls.n];
-            auto launch = [&]() {
-                return one ? launch_tiled_one(x.shape, c.p_storage, c.fast_math != 0, x.ls.h_descs[0],
-                                              0, 0, x.depth, c.tau, st)
-                           : launch_tiled(x.shape, c.p_storage, c.fast_math != 0, x.ls.d_tiles, nt,
-                                          x.ls.d_descs, 0, 0, x.depth, c.tau, st);
-            };
-            e = launch();
-            if (e == cudaSuccess) e = launch();
-            const int reps = 8;
+        for (size_t i = 0; i < cs.size() && e == cudaSuccess; ++i) {
+            e = cudaGraphLaunch(execs[i], st);  // warm
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+            if (e == cudaSuccess) e = cudaGraphLaunch(execs[i], st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) break;
-            x.cost = std::min(x.cost, (double)ms / (reps * x.depth * total_px));
+            if (e == cudaSuccess)
+                cs[i].cost = std::min(cs[i].cost, (double)ms / (kReps * cs[i].depth * total_px));
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (cudaGraphExec_t x : execs)
+        if (x) cudaGraphExecDestroy(x);
     release_all();
     if (e != cudaSuccess) return fail_cuda(e, "autotune launch");
     const Cand *best = &cs[0];
