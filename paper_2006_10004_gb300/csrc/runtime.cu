@@ -417,8 +417,12 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
     // Each candidate is timed as the run executes it: a CUDA graph of back-to-back launches
     // (direct launches would add a launch gap that graph replay does not have, and change the
     // ranking). Two rounds over all candidates, each candidate's cost the faster of its two:
-    // the first round also brings the GPU to its working clock.
-    constexpr int kReps = 8;
+    // the first round also brings the GPU to its working clock. A large set (several waves of
+    // tiles per launch) times well with fewer launches: one round of graphs of 2 launches, so
+    // that tuning stays a few launches per candidate.
+    const bool large = total_px > (double)(1 << 22);
+    const int kReps = large ? 2 : 8;
+    const int rounds = large ? 1 : 2;
     std::vector<cudaGraphExec_t> execs(cs.size(), nullptr);
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < cs.size() && e == cudaSuccess; ++i) {
@@ -441,7 +445,7 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    for (int round = 0; round < 2 && e == cudaSuccess; ++round) {
+    for (int round = 0; round < rounds && e == cudaSuccess; ++round) {
         for (size_t i = 0; i < cs.size() && e == cudaSuccess; ++i) {
             e = cudaGraphLaunch(execs[i], st);  // warm
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
