@@ -191,6 +191,28 @@ def resident_variants() -> list:
     return out
 
 
+_pinned_ok = None
+
+
+def _host_empty(shape, dtype) -> np.ndarray:
+    """An uninitialised host array (every element is written by the library), page-locked
+    through torch's caching host allocator when a CUDA device is present, else plain numpy."""
+    global _pinned_ok
+    if _pinned_ok is None:
+        try:
+            import torch
+
+            _pinned_ok = bool(torch.cuda.is_available())
+        except Exception:
+            _pinned_ok = False
+    if _pinned_ok:
+        import torch
+
+        tdt = {np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64}[np.dtype(dtype)]
+        return torch.empty(tuple(shape), dtype=tdt, pin_memory=True).numpy()
+    return np.empty(shape, dtype)
+
+
 def _is_torch_cuda(x) -> bool:
     return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
 
@@ -294,14 +316,15 @@ class Plan:
             if f.ndim != 2:
                 raise TypeError("f must be 2-D")
             H, W = f.shape
-            out = Result(bands=np.zeros((nb, H, W), np.float32), residual=np.zeros((H, W), np.float32),
-                         S=np.zeros((max(K - 1, 0),), np.float64))
+            # outputs in page-locked memory: the device-to-host copies run at full speed
+            out = Result(bands=_host_empty((nb, H, W), np.float32), residual=_host_empty((H, W), np.float32),
+                         S=_host_empty((max(K - 1, 0),), np.float64))
             if trace:
-                out["u"] = np.zeros((K + 1, H, W), np.float64)
+                out["u"] = _host_empty((K + 1, H, W), np.float64)
             if nf:
-                out["filtered"] = np.zeros((nf, H, W), np.float32)
+                out["filtered"] = _host_empty((nf, H, W), np.float32)
             if parseval:
-                out["S_parseval"] = np.zeros((max(K - 1, 1),), np.float64)
+                out["S_parseval"] = _host_empty((max(K - 1, 1),), np.float64)
             ptr = lambda a: a.ctypes.data
             kind = MEM_HOST
         keep.append(f)
