@@ -217,7 +217,8 @@ def run_gb300(args):
     if args.workload == "training":
         return run_training(args, tv, torch, local, ws)
     wl = _workload(args.workload)
-    plan = tv.Plan(local, **({"kernel": tv.KERNEL_TILED, "tile": args.tile} if args.tile >= 0 else {}))
+    plan = tv.Plan(local, acc_mode=args.acc_mode,
+                   **({"kernel": tv.KERNEL_TILED, "tile": args.tile} if args.tile >= 0 else {}))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -266,7 +267,8 @@ def run_gb300(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
               "data": "synthetic",
               "config": {"workload": wl.name, **shape_desc,
-                         "arith": "dual iterations f32, epilogue (u, phi, S, bands, residual) f64",
+                         "arith": "dual iterations f32, epilogue (u, phi, S, bands, residual) "
+                                  + ("f64" if args.acc_mode == 0 else "float-float (compensated f32), S f64"),
                          "l2": "flushed before every timed step (256 MiB write, untimed)",
                          "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                          "tile": st1["last_tile"], "temporal_block": st1["last_temporal_block"]},
@@ -353,6 +355,7 @@ def run_gb300(args):
                            "ms_per_decomp": ms, "Mpx_iter_per_s": m.px_iters / ms / 1e3}
         result["filter_bank_config1"] = measure_filters(tv, torch, plan, job, f_dev, stream, flush)
         result["inner_solvers"] = measure_solvers(tv, torch, plan, job, stream)
+        result["acc_mode_compare"] = measure_acc_modes(tv, torch, local, job, f_dev, stream, flush)
         result["batched_config2"] = measure_batched(tv, torch, local, 2, 1)
         result["training_crops"] = measure_crops(tv, torch, local)
         sv = measure_serving(tv, local, [float(args.serve_rate)], args.serve_requests)[0]
@@ -403,6 +406,28 @@ def measure_filters(tv, torch, plan, job, f_dev, stream, flush, n_filters: int =
     return {"filters": n_filters, "ms_with_filters": filt, "ms_without": plain,
             "overhead_frac": filt / plain - 1.0,
             "Mpx_iter_per_s_with_filters": job.px_iters / filt / 1e3}
+
+
+def measure_acc_modes(tv, torch, local, job, f_dev, stream, flush, reps: int = 3):
+    """Device time of the decomposition with the float64 epilogue and with the compensated
+    float32 (float-float) epilogue, L2 flushed before every timed run."""
+    out = {}
+    for mode in (0, 1):
+        with tv.Plan(local, acc_mode=mode) as p:
+            p.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for i in range(reps):
+                flush.fill_(i & 0xff)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                p.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            out[f"acc_mode_{mode}_ms"] = tot / reps
+    out["speedup_compensated"] = out["acc_mode_0_ms"] / out["acc_mode_1_ms"]
+    return out
 
 
 def measure_solvers(tv, torch, plan, job, stream, targets=(1e-4, 1e-5), check_every: int = 25):
@@ -505,7 +530,7 @@ ALG_FLOPS_PER_PX_ITER = 17
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def measure_crops(tv, torch, local, n: int = 3000, compare: bool = True):
+def measure_crops(tv, torch, local, n: int = 3000, compare: bool = True, acc_mode: int = 0):
     """Training-data generation: crops + standardisation over the set + decompositions
     (K = 50 steps of dt = .5, 300 iterations, 6 dyadic bands) of n 64x64 crops through
     tvspec_training_set (device memory); with ``compare``, against the same standardised crops
@@ -530,7 +555,7 @@ def measure_crops(tv, torch, local, n: int = 3000, compare: bool = True):
         return e0.elapsed_time(e1) / reps
 
     px_it = n * 64 * 64 * 50 * 300
-    with tv.Plan(local) as p:
+    with tv.Plan(local, acc_mode=acc_mode) as p:
         run = lambda: p.training_set(srcs_d, crops, 64, 1, 0.5, 50, 300, syn.DYADIC_EDGES, want_stats=False,
                                      stream=stream)
         s0 = p.stats()
@@ -555,7 +580,7 @@ def run_training(args, tv, torch, local, ws):
     dev = torch.device("cuda", local)
     torch.cuda.set_stream(torch.cuda.Stream(dev))
     with ClockSampler(local) as clk:
-        m = measure_crops(tv, torch, local, args.crops, compare=not args.quick)
+        m = measure_crops(tv, torch, local, args.crops, compare=not args.quick, acc_mode=args.acc_mode)
     t = m["training_set"]
     # the resident kernel is one launch per call and > 99 % of its device time (launch list in
     # profiles/); the call's event-timed duration bounds the kernel's from above
@@ -710,6 +735,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--crops", type=int, default=3000, help="crops of the training workload")
+    ap.add_argument("--acc-mode", type=int, default=0, choices=[0, 1],
+                    help="epilogue arithmetic: 0 float64, 1 compensated float32")
     ap.add_argument("--workload", default="config1",
                     choices=["config1", "m1024", "config2", "config3", "config4", "training"])
     ap.add_argument("--rates", default="20,50,100,200", help="config4: Poisson arrival rates (req/s)")

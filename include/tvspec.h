@@ -92,6 +92,16 @@ typedef struct {
     int resident_variant;   /* thread layout of the resident kernel: -1 (default) automatic,
                                else an index below tvspec_resident_variant_count(); an image the
                                variant cannot hold uses the automatic choice */
+    int acc_mode;           /* per-step epilogue arithmetic (u, phi, bands, residual, filters):
+                               0 (default) float64; 1 compensated float32 (float-float pairs,
+                               about 48 significant bits, on the float32 pipes, which GB300 runs
+                               many times faster than float64). S is reduced in float64 in both.
+                               Results are bit-identical across all paths within one mode. */
+    const char *tune_cache; /* optional path of a text file that keeps the autotuner's tile
+                               choices across processes: read when the plan is created (lines of
+                               another GPU model or library build are ignored), one line appended
+                               per new choice; NULL (default) = in-memory only. The string is
+                               copied by tvspec_plan_create. */
 } tvspec_config;
 
 /* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in

@@ -46,7 +46,8 @@ class Config(ctypes.Structure):
                 ("mem_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("pdl", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
                 ("test_barrier_noshow", ctypes.c_int), ("resident", ctypes.c_int),
-                ("resident_variant", ctypes.c_int)]
+                ("resident_variant", ctypes.c_int), ("acc_mode", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class Request(ctypes.Structure):
@@ -245,6 +246,8 @@ class Plan:
         for k, v in cfg.items():
             if not hasattr(c, k):
                 raise TypeError(f"unknown config field {k}")
+            if k == "tune_cache" and isinstance(v, str):
+                v = v.encode()
             setattr(c, k, v)
         self.config = c
         h = ctypes.c_void_p()
@@ -286,7 +289,52 @@ class Plan:
         fr = np.ascontiguousarray(np.asarray([float(r) for _, r in filters], np.float64))
         return nf, fH, fr
 
-    def _make_request(self, f, dt, K, n_inner, edges, trace, keep, filters=None, parseval=False):
+    @staticmethod
+    def _out_specs(nb, H, W, K, trace, nf, parseval):
+        """(name, shape, is_float64) of every output array of one request."""
+        specs = [("bands", (nb, H, W), False), ("residual", (H, W), False), ("S", (max(K - 1, 0),), True)]
+        if trace:
+            specs.append(("u", (K + 1, H, W), True))
+        if nf:
+            specs.append(("filtered", (nf, H, W), False))
+        if parseval:
+            specs.append(("S_parseval", (max(K - 1, 1),), True))
+        return specs
+
+    @staticmethod
+    def _alloc_outputs(spec_lists, device):
+        """Results for several requests carved out of one float32 and one float64 buffer (on
+        `device`, or page-locked host memory when device is None); views start 256-byte
+        aligned."""
+        import math as _m
+
+        tot = [0, 0]
+        offs = []
+        for specs in spec_lists:
+            o = []
+            for name, shape, f64 in specs:
+                al = 32 if f64 else 64
+                tot[f64] = (tot[f64] + al - 1) // al * al
+                o.append(tot[f64])
+                tot[f64] += int(_m.prod(shape))
+            offs.append(o)
+        if device is not None:
+            import torch
+
+            bufs = [torch.empty((max(tot[0], 1),), dtype=torch.float32, device=device),
+                    torch.empty((max(tot[1], 1),), dtype=torch.float64, device=device)]
+        else:
+            bufs = [_host_empty((max(tot[0], 1),), np.float32), _host_empty((max(tot[1], 1),), np.float64)]
+        results = []
+        for specs, o in zip(spec_lists, offs):
+            res = Result()
+            for (name, shape, f64), start in zip(specs, o):
+                n = int(_m.prod(shape))
+                res[name] = bufs[f64][start:start + n].reshape(shape)
+            results.append(res)
+        return results
+
+    def _make_request(self, f, dt, K, n_inner, edges, trace, keep, filters=None, parseval=False, out=None):
         e = self._edges(edges)
         keep.append(e)
         nb = len(e) - 1
@@ -299,16 +347,8 @@ class Plan:
             if f.dtype != torch.float32 or f.dim() != 2:
                 raise TypeError("f must be a 2-D float32 CUDA tensor")
             H, W = f.shape
-            dev = f.device
-            out = Result(bands=torch.empty((nb, H, W), dtype=torch.float32, device=dev),
-                         residual=torch.empty((H, W), dtype=torch.float32, device=dev),
-                         S=torch.empty((max(K - 1, 0),), dtype=torch.float64, device=dev))
-            if trace:
-                out["u"] = torch.empty((K + 1, H, W), dtype=torch.float64, device=dev)
-            if nf:
-                out["filtered"] = torch.empty((nf, H, W), dtype=torch.float32, device=dev)
-            if parseval:
-                out["S_parseval"] = torch.empty((max(K - 1, 1),), dtype=torch.float64, device=dev)
+            if out is None:
+                out = self._alloc_outputs([self._out_specs(nb, H, W, K, trace, nf, parseval)], f.device)[0]
             ptr = lambda t: t.data_ptr()
             kind = MEM_DEVICE
         else:
@@ -317,14 +357,8 @@ class Plan:
                 raise TypeError("f must be 2-D")
             H, W = f.shape
             # outputs in page-locked memory: the device-to-host copies run at full speed
-            out = Result(bands=_host_empty((nb, H, W), np.float32), residual=_host_empty((H, W), np.float32),
-                         S=_host_empty((max(K - 1, 0),), np.float64))
-            if trace:
-                out["u"] = _host_empty((K + 1, H, W), np.float64)
-            if nf:
-                out["filtered"] = _host_empty((nf, H, W), np.float32)
-            if parseval:
-                out["S_parseval"] = _host_empty((max(K - 1, 1),), np.float64)
+            if out is None:
+                out = self._alloc_outputs([self._out_specs(nb, H, W, K, trace, nf, parseval)], None)[0]
             ptr = lambda a: a.ctypes.data
             kind = MEM_HOST
         keep.append(f)
@@ -364,10 +398,22 @@ class Plan:
         """jobs: iterable of (f, dt, K, n_inner, edges[, filters]). Returns a list of Results."""
         keep = []
         reqs, outs, kinds = [], [], set()
+        jobs = list(jobs)
+        # all outputs of the batch carved out of one buffer per element type
+        specs = []
+        dev = None
         for job in jobs:
+            f, K, edges = job[0], int(job[2]), job[4]
+            flt = job[5] if len(job) > 5 else None
+            specs.append(self._out_specs(len(edges) - 1, f.shape[0], f.shape[1], K, trace,
+                                         len(flt) if flt else 0, parseval))
+            if _is_torch_cuda(f):
+                dev = f.device
+        pre = self._alloc_outputs(specs, dev) if jobs else []
+        for job, o_pre in zip(jobs, pre):
             f, dt, K, n_inner, edges = job[:5]
             r, o, k = self._make_request(f, dt, K, n_inner, edges, trace, keep,
-                                         job[5] if len(job) > 5 else None, parseval)
+                                         job[5] if len(job) > 5 else None, parseval, out=o_pre)
             reqs.append(r)
             outs.append(o)
             kinds.add(k)

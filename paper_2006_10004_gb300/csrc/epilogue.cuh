@@ -3,17 +3,22 @@
 // explicitly rounded intrinsic so all of them produce the same bits.
 #pragma once
 
+#include "ff_math.cuh"
 #include "tvspec_internal.h"
 
 namespace tvspec {
 
-// Divergence at (i, j) from float values of p with the negative-adjoint boundary terms:
-//   (div p)_ij = ([i<H-1] p1_ij - [i>0] p1_{i-1,j}) + ([j<W-1] p2_ij - [j>0] p2_{i,j-1}).
-__device__ __forceinline__ double div_at(int i, int j, int H, int W, float p1_ij, float p1_up,
-                                         float p2_ij, float p2_left) {
-    const double a = __dsub_rn(i < H - 1 ? (double)p1_ij : 0.0, i > 0 ? (double)p1_up : 0.0);
-    const double c = __dsub_rn(j < W - 1 ? (double)p2_ij : 0.0, j > 0 ? (double)p2_left : 0.0);
-    return __dadd_rn(a, c);
+// The four values of p that the divergence at (i, j) combines, with the negative-adjoint
+// boundary terms applied: (div p)_ij = (a1 - a0) + (b1 - b0), a1 = [i<H-1] p1_ij,
+// a0 = [i>0] p1_{i-1,j}, b1 = [j<W-1] p2_ij, b0 = [j>0] p2_{i,j-1}.
+struct DivTerms {
+    float a1, a0, b1, b0;
+};
+
+__device__ __forceinline__ DivTerms div_terms(int i, int j, int H, int W, float p1_ij, float p1_up,
+                                              float p2_ij, float p2_left) {
+    return {i < H - 1 ? p1_ij : 0.0f, i > 0 ? p1_up : 0.0f, j < W - 1 ? p2_ij : 0.0f,
+            j > 0 ? p2_left : 0.0f};
 }
 
 // Step k at pixel n (compact index) given div p there:
@@ -24,9 +29,15 @@ __device__ __forceinline__ double div_at(int i, int j, int H, int W, float p1_ij
 //   u_{k-1} in the ping-pong buffer.
 // Returns |phi_k| (0 at k = 0), g/dt of the next step in *gl_next and, when the Parseval-type
 // spectrum is requested, phi_k f in *phif (0 at k = 0).
-__device__ __forceinline__ double epilogue_pixel(const ImgDesc &d, int k, size_t n, double divp,
-                                                 float *gl_next, double *phif) {
+// acc_mode 0 computes in float64; acc_mode 1 in float-float (about 48 bits, on the float32
+// pipes: GB300's float64 rate is a small fraction of its float32 rate). |phi| and phi f are
+// returned as float64 either way; the S reductions are float64.
+__device__ __forceinline__ double epilogue_pixel_f64(const ImgDesc &d, int k, size_t n,
+                                                     const DivTerms &dv, float *gl_next,
+                                                     double *phif) {
     const size_t N = (size_t)d.H * d.W;
+    const double divp = __dadd_rn(__dsub_rn((double)dv.a1, (double)dv.a0),
+                                  __dsub_rn((double)dv.b1, (double)dv.b0));
     double *ucur = (k & 1) ? d.ub : d.ua;
     double *uoth = (k & 1) ? d.ua : d.ub;  // u_{k-1} in, u_{k+1} out
     const double uc = ucur[n];
@@ -71,6 +82,83 @@ __device__ __forceinline__ double epilogue_pixel(const ImgDesc &d, int k, size_t
     }
     uoth[n] = un;
     return absphi;
+}
+
+__device__ __forceinline__ double epilogue_pixel_ff(const ImgDesc &d, int k, size_t n,
+                                                    const DivTerms &dv, float *gl_next,
+                                                    double *phif) {
+    const size_t N = (size_t)d.H * d.W;
+    const ff dt = {d.ff_dt[0], d.ff_dt[1]};
+    const ff inv_dt = {d.ff_inv_dt[0], d.ff_inv_dt[1]};
+    const ff coef = {d.ff_coef[0], d.ff_coef[1]};
+    const ff divp = ff_add(ff_two_sum(dv.a1, -dv.a0), ff_two_sum(dv.b1, -dv.b0));
+    ff *ucur = reinterpret_cast<ff *>((k & 1) ? d.ub : d.ua);
+    ff *uoth = reinterpret_cast<ff *>((k & 1) ? d.ua : d.ub);
+    ff *accv = reinterpret_cast<ff *>(d.acc);
+    ff *faccv = reinterpret_cast<ff *>(d.facc);
+    const ff uc = ucur[n];
+    const ff un = ff_sub(uc, ff_mul(dt, divp));
+    if (!ff_isfinite(un)) atomicOr(d.status, kStatusNonFinite);
+    *gl_next = ff_to_float(ff_mul(un, inv_dt));
+    if (d.u_trace) d.u_trace[(size_t)(k + 1) * N + n] = ff_to_double(un);
+    double absphi = 0.0;
+    *phif = 0.0;
+    if (k >= 1) {
+        const ff up = uoth[n];
+        const ff tk = ff_mul(ff_from_float((float)k), dt);
+        const ff d2 = ff_add(ff_sub(un, ff_twice(uc)), up);
+        const ff phi = ff_mul(ff_mul(tk, d2), coef);
+        const double phid = ff_to_double(phi);
+        absphi = fabs(phid);
+        if (d.S_par) *phif = __dmul_rn(phid, (double)d.f[n]);
+        const int m = d.band_of_k[k];
+        const int mp = (k >= 2) ? d.band_of_k[k - 1] : -1;
+        ff acc = {0.0f, 0.0f};
+        if (mp >= 0) {
+            const ff old = accv[n];
+            if (mp == m) acc = old;
+            else d.bands[(size_t)mp * N + n] = ff_to_float(old);  // band mp is complete
+        }
+        if (m >= 0) acc = ff_add(acc, ff_mul(phi, dt));
+        const bool last = k == d.K - 1;
+        ff resid = {0.0f, 0.0f};
+        if (last) resid = ff_sub(uc, ff_mul(ff_mul(tk, ff_sub(un, uc)), inv_dt));
+        if (last) {
+            if (m >= 0) d.bands[(size_t)m * N + n] = ff_to_float(acc);
+            d.residual[n] = ff_to_float(resid);
+        } else {
+            accv[n] = acc;
+        }
+        for (int q = 0; q < d.n_filters; ++q) {
+            ff fa = (k >= 2) ? faccv[(size_t)q * N + n] : ff{0.0f, 0.0f};
+            const ff hq = ff_from_double(d.filt_H[(size_t)q * (d.K - 1) + (k - 1)]);
+            fa = ff_add(fa, ff_mul(ff_mul(hq, phi), dt));
+            if (last)
+                d.filtered[(size_t)q * N + n] =
+                    ff_to_float(ff_add(fa, ff_mul(ff_from_double(d.filt_res[q]), resid)));
+            else
+                faccv[(size_t)q * N + n] = fa;
+        }
+    }
+    uoth[n] = un;
+    return absphi;
+}
+
+__device__ __forceinline__ double epilogue_pixel(const ImgDesc &d, int k, size_t n,
+                                                 const DivTerms &dv, float *gl_next, double *phif) {
+    return d.acc_mode ? epilogue_pixel_ff(d, k, n, dv, gl_next, phif)
+                      : epilogue_pixel_f64(d, k, n, dv, gl_next, phif);
+}
+
+// u_0 = f at pixel n (Eq. TVflow) and g/dt of step 0; returns the latter.
+__device__ __forceinline__ float init_pixel(const ImgDesc &d, size_t n, float fv) {
+    if (d.acc_mode) {
+        reinterpret_cast<ff *>(d.ua)[n] = ff_from_float(fv);
+        return ff_to_float(ff_mul(ff_from_float(fv), ff{d.ff_inv_dt[0], d.ff_inv_dt[1]}));
+    }
+    const double u0 = (double)fv;
+    d.ua[n] = u0;
+    return (float)(u0 * d.inv_dt);
 }
 
 // Fixed-order sum of one double per thread over a block of kEpBlock threads: a shuffle tree

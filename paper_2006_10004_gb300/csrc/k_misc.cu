@@ -84,10 +84,8 @@ __global__ void __launch_bounds__(kEpBlock)
     const size_t n = (size_t)i * W + j;
     const float fv = d->f[n];
     if (!isfinite(fv)) atomicOr(d->status, kStatusNonFinite);
-    const double u0 = (double)fv;                      // u_0 = f  (Eq. TVflow)
-    d->ua[n] = u0;
-    d->gl[(size_t)i * d->pitch + j] = (float)(u0 * d->inv_dt);
-    if (d->u_trace) d->u_trace[n] = u0;
+    d->gl[(size_t)i * d->pitch + j] = init_pixel(*d, n, fv);  // u_0 = f  (Eq. TVflow)
+    if (d->u_trace) d->u_trace[n] = (double)fv;
 }
 
 cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_base,
@@ -122,11 +120,11 @@ __device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gs
         const P *p1 = static_cast<const P *>(d->p1[cp]);
         const P *p2 = static_cast<const P *>(d->p2[cp]);
         const size_t o = (size_t)i * pitch + j;
-        const double divp =
-            div_at(i, j, H, W, PStore<P>::load(p1[o]), i > 0 ? PStore<P>::load(p1[o - pitch]) : 0.0f,
-                   PStore<P>::load(p2[o]), j > 0 ? PStore<P>::load(p2[o - 1]) : 0.0f);
+        const DivTerms dv =
+            div_terms(i, j, H, W, PStore<P>::load(p1[o]), i > 0 ? PStore<P>::load(p1[o - pitch]) : 0.0f,
+                      PStore<P>::load(p2[o]), j > 0 ? PStore<P>::load(p2[o - 1]) : 0.0f);
         float gl_next;
-        absphi = epilogue_pixel(*d, k, (size_t)i * W + j, divp, &gl_next, &phif);
+        absphi = epilogue_pixel(*d, k, (size_t)i * W + j, dv, &gl_next, &phif);
         d->gl[o] = gl_next;
     }
     if (k < 1) return;  // no phi at step 0

@@ -132,10 +132,8 @@ __global__ void __launch_bounds__(32 * RW, MINB)
                     const size_t n = (size_t)y * W + c;
                     const float fv = d.f[n];
                     if (!isfinite(fv)) atomicOr(d.status, kStatusNonFinite);
-                    const double u0 = (double)fv;
-                    d.ua[n] = u0;
-                    if (d.u_trace) d.u_trace[n] = u0;
-                    g2[h] = (float)(u0 * d.inv_dt);
+                    g2[h] = init_pixel(d, n, fv);  // u_0 = f (Eq. TVflow)
+                    if (d.u_trace) d.u_trace[n] = (double)fv;
                 }
             }
             gl[r][j] = make_float2(g2[0], g2[1]);
@@ -196,10 +194,10 @@ __global__ void __launch_bounds__(32 * RW, MINB)
                         const size_t o = (size_t)y * pitch + c;
                         const float pv1 = h == 0 ? p1[r][j].x : p1[r][j].y;
                         const float pv2 = h == 0 ? p2[r][j].x : p2[r][j].y;
-                        const double divp = div_at(y, c, H, W, pv1, y > 0 ? gp1[o - pitch] : 0.0f,
-                                                   pv2, c > 0 ? gp2[o - 1] : 0.0f);
+                        const DivTerms dv = div_terms(y, c, H, W, pv1, y > 0 ? gp1[o - pitch] : 0.0f,
+                                                      pv2, c > 0 ? gp2[o - 1] : 0.0f);
                         double pf;
-                        const double a = epilogue_pixel(d, k, (size_t)y * W + c, divp, &g2[h], &pf);
+                        const double a = epilogue_pixel(d, k, (size_t)y * W + c, dv, &g2[h], &pf);
                         s_phi[(size_t)y * W + c] = a;
                         if (d.S_par) s_phif[(size_t)y * W + c] = pf;
                     }

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <sstream>
 
@@ -153,7 +154,7 @@ size_t slot_bytes_for(const Job &j, int storage, bool naive) {
 }
 
 tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStream_t st,
-                         bool async_alloc) {
+                         bool async_alloc, int acc_mode) {
     const tvspec_request &r = j.r;
     const bool trace = r.u_trace != nullptr;
     const int nb = r.n_edges - 1;
@@ -204,6 +205,7 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
     x.filt_res = (double *)(base + L.fres);
     x.facc = (double *)(base + L.facc);
     x.filtered = (float *)(base + L.filt);
+    x.acc_mode = acc_mode;
     x.S_par = par ? (double *)(base + L.spar) : nullptr;
     x.partials_par = par ? (double *)(base + L.ppar) : nullptr;
     x.ep_blocks = ep_blocks_for(r.H, r.W);
@@ -255,6 +257,18 @@ ImgDesc slot_desc(const Slot &s, int s0) {
     d.filtered = s.filtered;
     d.S_par = s.S_par;
     d.partials_par = s.partials_par;
+    d.acc_mode = s.acc_mode;
+    {
+        // float-float forms of dt, 1/dt, 1/dt^2 (hi = nearest float, lo = nearest float of the rest)
+        auto split = [](double v, float *out) {
+            out[0] = (float)v;
+            out[1] = (float)(v - (double)out[0]);
+        };
+        const double inv = 1.0 / s.dt;
+        split(s.dt, d.ff_dt);
+        split(inv, d.ff_inv_dt);
+        split(inv * inv, d.ff_coef);
+    }
     d.H = s.H;
     d.W = s.W;
     d.pitch = s.pitch;
@@ -348,6 +362,63 @@ static int default_depth(const tvspec_config &c, int shape) {
     if (c.temporal_block > 0) return std::min(c.temporal_block, TB);
     if (c.p_storage != TVSPEC_P_FP32) return std::min(8, TB);
     return TB;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tune cache file: lines "<prefix> <key> <shape> <depth>", prefix = GPU model, SM count and a
+// checksum of the tile-shape table, so that choices of another GPU or build are skipped.
+// ---------------------------------------------------------------------------------------------
+static std::string tune_prefix_for(int device) {
+    cudaDeviceProp prop{};
+    std::string name = "unknown";
+    int sms = 0;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) {
+        name = prop.name;
+        sms = prop.multiProcessorCount;
+    } else {
+        cudaGetLastError();
+    }
+    for (char &ch : name)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the shape table
+    for (int i = 0; i < tiled_shape_count(); ++i) {
+        const TileShape t = tiled_shape(i);
+        for (int v : {t.V, t.R, t.RW, t.TB}) {
+            h ^= (uint64_t)(v + 1);
+            h *= 1099511628211ull;
+        }
+    }
+    std::ostringstream o;
+    o << name << "/sm" << sms << "/shapes" << tiled_shape_count() << "-" << std::hex << h;
+    return o.str();
+}
+
+static void tune_cache_load(tvspec_plan *plan) {
+    if (plan->tune_cache.empty()) return;
+    FILE *fp = std::fopen(plan->tune_cache.c_str(), "r");
+    if (!fp) return;
+    char line[4096];
+    while (std::fgets(line, sizeof(line), fp)) {
+        std::istringstream in(line);
+        std::string prefix, key;
+        int shape = -1, depth = 0;
+        if (!(in >> prefix >> key >> shape >> depth)) continue;
+        if (prefix != plan->tune_prefix) continue;
+        if (shape < 0 || shape >= tiled_shape_count() || depth < 1 || depth > tiled_shape(shape).TB)
+            continue;
+        plan->tune[key] = {shape, depth};
+    }
+    std::fclose(fp);
+}
+
+static void tune_cache_append(tvspec_plan *plan, const std::string &key, int shape, int depth) {
+    if (plan->tune_cache.empty() || key.size() > 3500) return;  // lines stay below 4 KB
+    static std::mutex file_mu;  // plans of one process append whole lines
+    std::lock_guard<std::mutex> lk(file_mu);
+    FILE *fp = std::fopen(plan->tune_cache.c_str(), "a");
+    if (!fp) return;  // the cache is an optimisation: an unwritable file is not an error
+    std::fprintf(fp, "%s %s %d %d\n", plan->tune_prefix.c_str(), key.c_str(), shape, depth);
+    std::fclose(fp);
 }
 
 tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, cudaStream_t st,
@@ -468,6 +539,7 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
     for (const Cand &x : cs)
         if (x.cost < best->cost) best = &x;
     plan->tune[key.str()] = {best->shape, best->depth};
+    tune_cache_append(plan, key.str(), best->shape, best->depth);
     *shape = best->shape;
     *depth = best->depth;
     return TVSPEC_OK;
@@ -610,7 +682,7 @@ static void free_entry(CacheEntry &E, cudaStream_t st) {
 static std::string job_key(const tvspec_config &c, const std::vector<Job> &jobs) {
     std::ostringstream k;
     k << c.p_storage << '/' << c.warm_start << '/' << c.tau << '/' << c.kernel << '/' << c.tile
-      << '/' << c.temporal_block << '/' << c.fast_math << '/' << c.use_graphs;
+      << '/' << c.temporal_block << '/' << c.fast_math << '/' << c.use_graphs << '/' << c.acc_mode;
     k.precision(17);
     for (const Job &j : jobs) {
         k << ';' << j.r.H << 'x' << j.r.W << ',' << j.r.K << ',' << j.r.n_inner << ',' << j.r.dt
@@ -671,7 +743,7 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
     for (int i = 0; i < n; ++i) {
         Slot s;
         tvspec_status st = slot_alloc(&s, jobs[E->order[i]], plan->cfg.p_storage, naive,
-                                      plan->stream, false);
+                                      plan->stream, false, plan->cfg.acc_mode);
         if (st != TVSPEC_OK) {
             free_entry(*E, plan->stream);
             return st;
@@ -1019,6 +1091,7 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
     if (c.max_batch < 0) return fail(TVSPEC_EINVAL, "max_batch must be >= 0");
     if (c.barrier_timeout_ms < 1) return fail(TVSPEC_EINVAL, "barrier_timeout_ms must be >= 1");
     if (c.resident < 0 || c.resident > 2) return fail(TVSPEC_EINVAL, "resident must be 0, 1 or 2");
+    if (c.acc_mode < 0 || c.acc_mode > 1) return fail(TVSPEC_EINVAL, "acc_mode must be 0 or 1");
     if (c.resident_variant < -1 || c.resident_variant >= resident_variant_count())
         return fail(TVSPEC_EINVAL, "resident_variant out of range");
     int n_dev = 0;
@@ -1033,6 +1106,10 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
     if (!p) return fail(TVSPEC_ENOMEM, "plan allocation");
     p->device = device;
     p->cfg = c;
+    if (c.tune_cache) p->tune_cache = c.tune_cache;
+    p->cfg.tune_cache = nullptr;  // the plan keeps its own copy of the path
+    p->tune_prefix = tune_prefix_for(device);
+    tune_cache_load(p);
     e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete p;

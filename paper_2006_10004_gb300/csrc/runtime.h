@@ -58,12 +58,13 @@ struct Slot {
     double *filt_H = nullptr, *filt_res = nullptr, *facc = nullptr;
     float *filtered = nullptr;
     double *S_par = nullptr, *partials_par = nullptr;  // Parseval-type spectrum, if requested
+    int acc_mode = 0;  // epilogue arithmetic (tvspec_config::acc_mode)
     int ep_blocks = 0;
     size_t p_bytes = 0;  // bytes of one pitched p array (one component, one copy)
 };
 size_t slot_bytes_for(const Job &j, int storage, bool naive);
 tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStream_t st,
-                         bool async_alloc);
+                         bool async_alloc, int acc_mode = 0);
 void slot_free(Slot *s, cudaStream_t st);
 ImgDesc slot_desc(const Slot &s, int s0);
 
@@ -115,6 +116,8 @@ struct tvspec_plan {
     std::mutex mu;  // serialises the plain and batched paths
     std::list<std::unique_ptr<tvspec::CacheEntry>> cache;  // most recent first
     std::map<std::string, std::pair<int, int>> tune;         // key -> (shape, depth)
+    std::string tune_cache;   // file keeping tune across processes ("" = none)
+    std::string tune_prefix;  // this GPU model and shape table, first field of the file lines
     std::map<std::string, std::unique_ptr<tvspec::LaunchSet>> iter_sets;
     std::list<tvspec::Slot> scratch;                        // buffers of tvspec_rof_step etc.
     std::atomic<uint64_t> kernel_launches{0}, graph_launches{0}, graphs_built{0},

@@ -209,7 +209,7 @@ void Server::loop() {
         // admission: workspace, image upload
         std::vector<std::shared_ptr<ServeReq>> started;
         for (auto &r : admitted) {
-            tvspec_status s = slot_alloc(&r->slot, r->job, c.p_storage, false, st, true);
+            tvspec_status s = slot_alloc(&r->slot, r->job, c.p_storage, false, st, true, c.acc_mode);
             if (s == TVSPEC_OK) {
                 cudaError_t e = cudaMemsetAsync(r->slot.base + r->slot.zero_off, 0, r->slot.zero_bytes, st);
                 if (e == cudaSuccess)

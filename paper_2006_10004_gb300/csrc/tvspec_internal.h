@@ -41,6 +41,9 @@ struct ImgDesc {
     const double *filt_res; // n_filters residual weights
     double *facc;           // n_filters x H x W running filter sums (compact)
     float *filtered;        // n_filters x H x W output (compact), device
+    int acc_mode;           // 0: float64 epilogue; 1: compensated float32 (float-float); the
+                            // u, acc and facc arrays then hold (hi, lo) float pairs
+    float ff_dt[2], ff_inv_dt[2], ff_coef[2];  // dt, 1/dt, 1/dt^2 as float-float (acc_mode 1)
     double *S_par;          // K-1 values <phi_k, f>, or nullptr (not requested)
     double *partials_par;   // per-epilogue-block partial sums of phi_k f
     int H, W, pitch;

@@ -388,3 +388,22 @@ def test_invalid_arguments_leave_plan_usable(plan, tv):
         plan.decompose(bad, 0.5, 4, 10, syn.DYADIC_EDGES)
     out = plan.decompose(f, 0.5, 4, 10, syn.DYADIC_EDGES)
     assert np.all(np.isfinite(out["bands"]))
+
+
+def test_tune_cache_file_round_trip(tv, tmp_path):
+    # the first plan tunes and appends its choice; a later plan reads choices from the file
+    path = str(tmp_path / "tune.txt")
+    f = _img(40, 60, 3)
+    args = (f, 0.5, 4, 16, syn.DYADIC_EDGES)
+    with tv.Plan(0, tune_cache=path) as a:
+        ra = a.decompose(*args)
+    lines = open(path).read().split("\n")
+    prefix, key, shape, depth = lines[0].split()
+    forced = 3 if int(shape) != 3 else 2
+    with open(path, "w") as fh:
+        fh.write(f"{prefix} {key} {forced} 4\n")
+        fh.write(f"another-gpu/sm1/shapes1-0 {key} 0 1\n")  # ignored: other GPU / build
+    with tv.Plan(0, tune_cache=path) as b:
+        rb = b.decompose(*args)
+        assert b.stats()["last_tile"] == forced
+    _same(ra, rb)  # every tile shape gives the same bits
