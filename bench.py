@@ -336,6 +336,17 @@ def run_gb300(args):
         v, el, K, cores = _oracle_sample(job, args.cpu_k)
         result["cpu_baseline"] = {"value": v, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
                                   "sample": f"first {K} of {job.K} ROF steps of the same image ({el:.1f} s)"}
+        # the same oracle on one core, on a shorter sample
+        import oracle
+
+        oracle.set_threads(1)
+        v1, el1, K1, _ = _oracle_sample(job, max(1, args.cpu_k // 10))
+        oracle.set_threads(cores)
+        result["cpu_baseline"]["single_thread"] = {
+            "value": v1, "cores": 1, "sample": f"first {K1} of {job.K} ROF steps ({el1:.1f} s)"}
+
+    if rank == 0 and not args.quick and args.workload == "config3":
+        result["precision_study"] = measure_precision(tv, torch, local, job, f_dev, stream)
 
     if rank == 0 and not args.quick and args.workload == "config1":
         # the other two parts of the metric: 1024^2 decompositions/s and served p50/p99,
@@ -406,6 +417,34 @@ def measure_filters(tv, torch, plan, job, f_dev, stream, flush, n_filters: int =
     return {"filters": n_filters, "ms_with_filters": filt, "ms_without": plain,
             "overhead_frac": filt / plain - 1.0,
             "Mpx_iter_per_s_with_filters": job.px_iters / filt / 1e3}
+
+
+def measure_precision(tv, torch, local, job, f_dev, stream):
+    """Config 3's precision study: the dual field stored as fp32 / fp16 / bf16 / snorm16 between
+    launches. Per storage: device time of one decomposition and the bands' and residual's
+    deviation from the fp32 run (L-inf relative to max|f|, relative L2)."""
+    out = {}
+    ref = None
+    fmax = float(f_dev.abs().max())
+    for name, st_kind in (("fp32", 0), ("fp16", 1), ("bf16", 2), ("snorm16", 3)):
+        with tv.Plan(local, p_storage=st_kind) as p:
+            r = p.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = p.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            row = {"ms": a.elapsed_time(b), "tile": p.stats()["last_tile"]}
+        if ref is None:
+            ref = r
+        else:
+            db = (r["bands"].double() - ref["bands"].double())
+            row["bands_inf_rel_maxf"] = float(db.abs().max()) / fmax
+            row["bands_rel_l2"] = float(db.norm() / ref["bands"].double().norm())
+            row["residual_inf_rel_maxf"] = float((r["residual"] - ref["residual"]).abs().max()) / fmax
+        out[name] = row
+    return out
 
 
 def measure_acc_modes(tv, torch, local, job, f_dev, stream, flush, reps: int = 3):
@@ -495,11 +534,22 @@ def measure_batched(tv, torch, local, steps: int, warmup: int, with_clocks=None)
     s1 = plan.stats()
     n_plain = max(1, steps // 2)
     t_plain = timed(plain, n_plain)
+    # the plain form without graph replay: one image at a time, every launch from the host
+    nograph = tv.Plan(local, use_graphs=0)
+
+    def plain_nograph():
+        for j in jobs:
+            nograph.decompose(*j, stream=stream)
+
+    plain_nograph()
+    t_nograph = timed(plain_nograph, 1)
+    nograph.close()
     n_img = len(jobs)
     out = {"workload": wl.name, "images": n_img, "px_iters_per_batch": wl.px_iters,
            "batched_images_per_s": n_img * steps / t_batch, "batched_ms": 1000 * t_batch / steps,
            "batched_Mpx_iter_per_s": wl.px_iters * steps / t_batch / 1e6,
            "plain_images_per_s": n_img * n_plain / t_plain, "plain_ms": 1000 * t_plain / n_plain,
+           "plain_no_graph_images_per_s": n_img / t_nograph,
            "tile": s1["last_tile"], "temporal_block": s1["last_temporal_block"],
            "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"])}
     out["batched_over_plain"] = out["batched_images_per_s"] / out["plain_images_per_s"]

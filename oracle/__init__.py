@@ -94,6 +94,8 @@ def _lib():
             h.orc_pdhg.restype = ctypes.c_int
             h.orc_rof_gap_pair.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
             h.orc_rof_gap_pair.restype = ctypes.c_double
+            h.orc_set_threads.argtypes = [ctypes.c_int]
+            h.orc_set_threads.restype = ctypes.c_int
             h.orc_max_threads.argtypes = []
             h.orc_max_threads.restype = ctypes.c_int
             _handle = h
@@ -106,6 +108,11 @@ def _f64(a) -> np.ndarray:
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of later calls (n >= 1); returns the new count."""
+    return int(_lib().orc_set_threads(int(n)))
 
 
 def max_threads() -> int:

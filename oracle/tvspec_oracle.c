@@ -46,6 +46,19 @@
 
 #define IDX(i, j) ((size_t)(i) * (size_t)W + (size_t)(j))
 
+/* Sets the number of OpenMP threads later calls use (n >= 1); returns the new maximum. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

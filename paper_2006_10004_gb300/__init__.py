@@ -25,7 +25,7 @@ STATUS = {0: "TVSPEC_OK", 1: "TVSPEC_EINVAL", 2: "TVSPEC_ENOMEM", 3: "TVSPEC_ECU
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTREADY, ECANCELLED, ENOTSUP = range(8)
 SOLVER_CHAMBOLLE, SOLVER_FGP, SOLVER_PDHG = range(3)
 SOLVERS = {"chambolle": SOLVER_CHAMBOLLE, "fgp": SOLVER_FGP, "pdhg": SOLVER_PDHG}
-P_FP32, P_FP16, P_BF16 = 0, 1, 2
+P_FP32, P_FP16, P_BF16, P_SNORM16 = 0, 1, 2, 3
 MEM_HOST, MEM_DEVICE = 0, 1
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_TILED = 0, 1, 2
 

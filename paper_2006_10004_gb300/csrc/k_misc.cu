@@ -58,6 +58,7 @@ cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void
         case 0: return naive_typed<float>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
         case 1: return naive_typed<__half>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
         case 2: return naive_typed<__nv_bfloat16>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
+        case 3: return naive_typed<short>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -201,6 +202,7 @@ cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_i
         case 0: return cudaLaunchKernelEx(&cfg, k_epilogue<float>, dd, ep_img, ep_base, gstep, depth);
         case 1: return cudaLaunchKernelEx(&cfg, k_epilogue<__half>, dd, ep_img, ep_base, gstep, depth);
         case 2: return cudaLaunchKernelEx(&cfg, k_epilogue<__nv_bfloat16>, dd, ep_img, ep_base, gstep, depth);
+        case 3: return cudaLaunchKernelEx(&cfg, k_epilogue<short>, dd, ep_img, ep_base, gstep, depth);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -221,6 +223,7 @@ cudaError_t launch_epilogue_one(int p_storage, const ImgDesc &d, int gstep, int 
         case 0: return cudaLaunchKernelEx(&cfg, k_epilogue_one<float>, d, gstep, depth);
         case 1: return cudaLaunchKernelEx(&cfg, k_epilogue_one<__half>, d, gstep, depth);
         case 2: return cudaLaunchKernelEx(&cfg, k_epilogue_one<__nv_bfloat16>, d, gstep, depth);
+        case 3: return cudaLaunchKernelEx(&cfg, k_epilogue_one<short>, d, gstep, depth);
         default: return cudaErrorInvalidValue;
     }
 }

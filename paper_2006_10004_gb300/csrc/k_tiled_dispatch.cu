@@ -6,6 +6,7 @@ namespace tvspec {
 TiledKernel tiled_kernel_f32(int shape, bool fast);
 TiledKernel tiled_kernel_f16(int shape, bool fast);
 TiledKernel tiled_kernel_bf16(int shape, bool fast);
+TiledKernel tiled_kernel_s16(int shape, bool fast);
 TiledOneKernel tiled_one_kernel_f32(int shape, bool fast);
 
 #define TVSPEC_SHAPE_ROW(idx, V, R, RW, TB, MINB) {V, R, RW, TB},
@@ -32,6 +33,7 @@ cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *til
         case 0: k = tiled_kernel_f32(shape, fast); break;
         case 1: k = tiled_kernel_f16(shape, fast); break;
         case 2: k = tiled_kernel_bf16(shape, fast); break;
+        case 3: k = tiled_kernel_s16(shape, fast); break;
         default: return cudaErrorInvalidValue;
     }
     if (!k) return cudaErrorInvalidValue;

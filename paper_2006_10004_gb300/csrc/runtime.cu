@@ -1082,7 +1082,7 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
     *out = nullptr;
     tvspec_config c;
     if (cfg) c = *cfg; else tvspec_config_init(&c);
-    if (c.p_storage < 0 || c.p_storage > 2) return fail(TVSPEC_EINVAL, "p_storage out of range");
+    if (c.p_storage < 0 || c.p_storage > 3) return fail(TVSPEC_EINVAL, "p_storage out of range");
     if (!(c.tau > 0.0f) || !(c.tau <= 0.25f)) return fail(TVSPEC_EINVAL, "tau must be in (0, 0.25]");
     if (c.kernel < 0 || c.kernel > 2) return fail(TVSPEC_EINVAL, "kernel out of range");
     if (c.tile < -1 || c.tile >= tiled_shape_count()) return fail(TVSPEC_EINVAL, "tile out of range");

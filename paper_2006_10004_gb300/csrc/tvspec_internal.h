@@ -86,6 +86,17 @@ template <> struct PStore<__nv_bfloat16> {
     static __device__ __forceinline__ float load(__nv_bfloat16 x) { return __bfloat162float(x); }
     static __device__ __forceinline__ __nv_bfloat16 store(float x) { return __float2bfloat16_rn(x); }
 };
+// SNORM16: the dual field lies in the unit ball (|p| <= 1), so a 16-bit signed fixed-point
+// value q / 32767 covers it with a uniform step of 1/32767 (half a step of rounding error).
+template <> struct PStore<short> {
+    static __device__ __forceinline__ float load(short x) {
+        return __fmul_rn(__int2float_rn((int)x), 1.0f / 32767.0f);
+    }
+    static __device__ __forceinline__ short store(float x) {
+        const float c = fminf(fmaxf(x, -1.0f), 1.0f);
+        return (short)__float2int_rn(__fmul_rn(c, 32767.0f));
+    }
+};
 
 // ---- launchers (defined in the .cu files) -------------------------------------------------
 
@@ -103,7 +114,7 @@ void tiled_output_tile(const TileShape &s, int *ow, int *oh);
 
 // Launch one tiled pass of global step gstep: every CTA advances its tile by
 // min(depth, n_inner - blk depth) iterations (depth <= the shape's TB), reading copy
-// p_copy(k, nb, blk) of the dual field and writing the other. p_storage: 0 fp32, 1 fp16, 2 bf16.
+// p_copy(k, nb, blk) of the dual field and writing the other. p_storage: 0 fp32, 1 fp16, 2 bf16, 3 snorm16.
 // With pdl, the launch may start while the preceding kernel in the stream drains
 // (programmatic dependent launch); the kernels wait for it before touching any data.
 cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *tiles, int n_tiles,

@@ -329,9 +329,9 @@ def test_config3_full_run_properties(plan):
     assert np.array_equal(b["bands"], 2 * a["bands"]) and np.array_equal(b["S"], a["S"])
 
 
-@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("storage", [1, 2, 3])
 def test_16bit_dual_storage_reports_error(tv, storage):
-    # fp16 / bf16 storage of p between launches: errors are reported, no bar is promised;
+    # fp16 / bf16 / snorm16 storage of p between launches: errors are reported, no bar is promised;
     # the reconstruction identity holds regardless (it telescopes in float64)
     job = syn.config1(H=256, W=256, K=20).jobs[0]
     with tv.Plan(0, p_storage=storage) as p:
