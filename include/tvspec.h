@@ -286,7 +286,12 @@ tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float
  *                            family of the GPU toolbox timed in Sec. 4.3); accelerated when
  *                            pdhg_gamma > 0 (steps tau_n, sigma_n, theta_n updated per
  *                            iteration), basic with theta = 1 when pdhg_gamma == 0. */
-enum { TVSPEC_SOLVER_CHAMBOLLE = 0, TVSPEC_SOLVER_FGP = 1, TVSPEC_SOLVER_PDHG = 2 };
+enum {
+    TVSPEC_SOLVER_CHAMBOLLE = 0,
+    TVSPEC_SOLVER_FGP = 1,           /* temporally blocked register tiles, 8 iterations per launch */
+    TVSPEC_SOLVER_PDHG = 2,
+    TVSPEC_SOLVER_FGP_REFERENCE = 3  /* FGP one iteration per launch (same results as FGP) */
+};
 
 typedef struct tvspec_rof_request {
     const float *g;         /* in: H*W image (mem_kind memory) */

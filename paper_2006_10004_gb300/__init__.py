@@ -23,8 +23,9 @@ __all__ = ["Plan", "Config", "TvSpecError", "load", "build", "STATUS"]
 STATUS = {0: "TVSPEC_OK", 1: "TVSPEC_EINVAL", 2: "TVSPEC_ENOMEM", 3: "TVSPEC_ECUDA",
           4: "TVSPEC_ETIMEOUT", 5: "TVSPEC_ENOTREADY", 6: "TVSPEC_ECANCELLED", 7: "TVSPEC_ENOTSUP"}
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTREADY, ECANCELLED, ENOTSUP = range(8)
-SOLVER_CHAMBOLLE, SOLVER_FGP, SOLVER_PDHG = range(3)
-SOLVERS = {"chambolle": SOLVER_CHAMBOLLE, "fgp": SOLVER_FGP, "pdhg": SOLVER_PDHG}
+SOLVER_CHAMBOLLE, SOLVER_FGP, SOLVER_PDHG, SOLVER_FGP_REFERENCE = range(4)
+SOLVERS = {"chambolle": SOLVER_CHAMBOLLE, "fgp": SOLVER_FGP, "pdhg": SOLVER_PDHG,
+           "fgp_reference": SOLVER_FGP_REFERENCE}
 P_FP32, P_FP16, P_BF16, P_SNORM16 = 0, 1, 2, 3
 MEM_HOST, MEM_DEVICE = 0, 1
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_TILED = 0, 1, 2

@@ -3,9 +3,11 @@
 // gradient projection (FGP) on the same dual, and Chambolle and Pock's primal-dual hybrid
 // gradient (PDHG), with the duality gap of the returned primal-dual pair.
 //
-// FGP and PDHG run one iteration per launch (PDHG: a dual and a primal launch) on pitched
-// float32 arrays, one thread per pixel; their scalar step sequences (momentum, steps) are
-// computed in float64 on the host. The gap is reduced in float64 over a fixed partition.
+// FGP runs temporally blocked in register tiles like the Chambolle kernel (a one-iteration-
+// per-launch reference kernel gives the same bits); PDHG runs one iteration per launch (a dual
+// and a primal launch) on pitched float32 arrays, one thread per pixel. The scalar step
+// sequences (momentum, steps) are computed in float64 on the host. The gap is reduced in
+// float64 over a fixed partition.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -27,7 +29,30 @@ __device__ __forceinline__ float divergence(const float *p1, const float *p2, in
     return a + b;
 }
 
-// One FGP iteration: p_new = Pi(r + grad(div r - g/lambda) / 8); r_out = p_new + beta (p_new - p).
+// The FGP update of one pixel given w = div r - g/lambda there and its masked forward
+// differences G: q = r + G / 8, p_new = q / max(1, |q|), r_new = p_new + beta (p_new - p).
+// Explicitly rounded, so the one-iteration and the tiled kernels agree bit for bit.
+__device__ __forceinline__ void fgp_pixel(float &p1, float &p2, float &r1, float &r2, float G1,
+                                          float G2, float beta) {
+    float q1 = __fadd_rn(r1, __fmul_rn(G1, 0.125f));
+    float q2 = __fadd_rn(r2, __fmul_rn(G2, 0.125f));
+    const float n = __fsqrt_rn(__fadd_rn(__fmul_rn(q1, q1), __fmul_rn(q2, q2)));
+    if (n > 1.0f) {
+        q1 = __fdiv_rn(q1, n);
+        q2 = __fdiv_rn(q2, n);
+    }
+    r1 = __fadd_rn(q1, __fmul_rn(beta, __fsub_rn(q1, p1)));
+    r2 = __fadd_rn(q2, __fmul_rn(beta, __fsub_rn(q2, p2)));
+    p1 = q1;
+    p2 = q2;
+}
+
+// w = (r1 - r1_up) + (r2 - r2_left) - g/lambda, explicitly rounded.
+__device__ __forceinline__ float fgp_w(float r1, float r1u, float r2, float r2l, float gl) {
+    return __fsub_rn(__fadd_rn(__fsub_rn(r1, r1u), __fsub_rn(r2, r2l)), gl);
+}
+
+// One FGP iteration per launch, one thread per pixel, neighbours from global memory.
 __global__ void __launch_bounds__(kSolverBlockX * kSolverBlockY)
     k_fgp(float *__restrict__ p1, float *__restrict__ p2, const float *__restrict__ r1,
           const float *__restrict__ r2, float *__restrict__ r1o, float *__restrict__ r2o,
@@ -36,20 +61,130 @@ __global__ void __launch_bounds__(kSolverBlockX * kSolverBlockY)
     const int i = blockIdx.y * kSolverBlockY + threadIdx.y;
     if (i >= H || j >= W) return;
     const size_t o = (size_t)i * pitch + j;
-    const float w = divergence(r1, r2, i, j, H, W, pitch) - gl[o];
-    const float G1 = i < H - 1 ? (divergence(r1, r2, i + 1, j, H, W, pitch) - gl[o + pitch]) - w : 0.0f;
-    const float G2 = j < W - 1 ? (divergence(r1, r2, i, j + 1, H, W, pitch) - gl[o + 1]) - w : 0.0f;
-    float q1 = r1[o] + G1 * 0.125f, q2 = r2[o] + G2 * 0.125f;
-    const float n = sqrtf(q1 * q1 + q2 * q2);
-    if (n > 1.0f) {
-        q1 = q1 / n;
-        q2 = q2 / n;
-    }
-    r1o[o] = q1 + beta * (q1 - p1[o]);
-    r2o[o] = q2 + beta * (q2 - p2[o]);
-    p1[o] = q1;
-    p2[o] = q2;
+    auto w_at = [&](int y, int x) {
+        const size_t q = (size_t)y * pitch + x;
+        return fgp_w(r1[q], y > 0 ? r1[q - pitch] : 0.0f, r2[q], x > 0 ? r2[q - 1] : 0.0f, gl[q]);
+    };
+    const float w = w_at(i, j);
+    const float G1 = i < H - 1 ? __fsub_rn(w_at(i + 1, j), w) : 0.0f;
+    const float G2 = j < W - 1 ? __fsub_rn(w_at(i, j + 1), w) : 0.0f;
+    float a1 = p1[o], a2 = p2[o], b1 = r1[o], b2 = r2[o];
+    fgp_pixel(a1, a2, b1, b2, G1, G2, beta);
+    r1o[o] = b1;
+    r2o[o] = b2;
+    p1[o] = a1;
+    p2[o] = a2;
 }
+
+// Temporally blocked FGP: a CTA holds a (RW R) x (32 V) tile of p, r and g/lambda in registers
+// (lane l of warp wy: columns [lV, lV + V) of rows [wy R, wy R + R)), runs up to TB iterations
+// and stores the centre (halo TB rows and roundup(TB, V) columns each side, recomputed by the
+// neighbouring tiles: one iteration reads r at the offsets of the Chambolle iteration). Row
+// neighbours come from registers or a warp shuffle, column neighbours across warps from two
+// shared-memory rows (the bottom row of r1, the top row of w) with two CTA barriers per
+// iteration. beta[k] is the momentum of iteration k of the launch. Pixels outside the image are
+// zero and their differences masked, which realises the Neumann boundary.
+struct FgpBetas {
+    float v[16];
+};
+
+struct FgpDesc {
+    const float *gl;
+    float *p1[2], *p2[2], *r1[2], *r2[2];
+    int H, W, pitch;
+};
+
+template <int V, int R, int RW, int TB>
+__global__ void __launch_bounds__(32 * RW, 1)
+    k_fgp_tiled(const __grid_constant__ FgpDesc d, int ntx, int src, int n_iter,
+                const __grid_constant__ FgpBetas betas) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int TW = 32 * V, TH = RW * R;
+    constexpr int HX = (TB + V - 1) / V * V;
+    constexpr int OW = TW - 2 * HX, OH = TH - 2 * TB;
+    static_assert(OW > 0 && OH > 0 && R * V <= 32, "tile");
+    __shared__ float s_r1b[RW][TW];
+    __shared__ float s_wt[RW][TW];
+    const int H = d.H, W = d.W, pitch = d.pitch;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+    const int x0 = tx * OW, y0 = ty * OH;
+    const int cx = x0 - HX + lane * V, ry = y0 - TB + wy * R;
+    float p1[R][V], p2[R][V], r1[R][V], r2[R][V], gl[R][V];
+    unsigned m1 = 0u, m2 = 0u;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = ry + r;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int c = cx + v;
+            const bool in = y >= 0 && y < H && c >= 0 && c < W;
+            const size_t o = (size_t)y * pitch + c;
+            p1[r][v] = in ? d.p1[src][o] : 0.0f;
+            p2[r][v] = in ? d.p2[src][o] : 0.0f;
+            r1[r][v] = in ? d.r1[src][o] : 0.0f;
+            r2[r][v] = in ? d.r2[src][o] : 0.0f;
+            gl[r][v] = in ? d.gl[o] : 0.0f;
+            if (in && y < H - 1) m1 |= 1u << (r * V + v);
+            if (in && c < W - 1) m2 |= 1u << (r * V + v);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) s_r1b[wy][lane * V + v] = r1[R - 1][v];
+    __syncthreads();
+    for (int it = 0; it < n_iter; ++it) {
+        const float beta = betas.v[it];
+        float w[R][V];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float left = __shfl_up_sync(FULL, r2[r][V - 1], 1);  // lane 0: halo, unused
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float up = r > 0 ? r1[r - 1][v] : (wy > 0 ? s_r1b[wy - 1][lane * V + v] : 0.0f);
+                const float lf = v > 0 ? r2[r][v - 1] : left;
+                w[r][v] = fgp_w(r1[r][v], up, r2[r][v], lf, gl[r][v]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) s_wt[wy][lane * V + v] = w[0][v];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float right = __shfl_down_sync(FULL, w[r][0], 1);  // lane 31: halo, unused
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float wd = r < R - 1 ? w[r + 1][v] : (wy < RW - 1 ? s_wt[wy + 1][lane * V + v] : w[r][v]);
+                const float wr = v < V - 1 ? w[r][v + 1] : right;
+                const int b = r * V + v;
+                const float G1 = ((m1 >> b) & 1u) ? __fsub_rn(wd, w[r][v]) : 0.0f;
+                const float G2 = ((m2 >> b) & 1u) ? __fsub_rn(wr, w[r][v]) : 0.0f;
+                fgp_pixel(p1[r][v], p2[r][v], r1[r][v], r2[r][v], G1, G2, beta);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) s_r1b[wy][lane * V + v] = r1[R - 1][v];
+        __syncthreads();
+    }
+    // the exact centre into the other copy
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = ry + r;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int c = cx + v;
+            if (y >= y0 && y < y0 + OH && y < H && c >= x0 && c < x0 + OW && c < W) {
+                const size_t o = (size_t)y * pitch + c;
+                d.p1[src ^ 1][o] = p1[r][v];
+                d.p2[src ^ 1][o] = p2[r][v];
+                d.r1[src ^ 1][o] = r1[r][v];
+                d.r2[src ^ 1][o] = r2[r][v];
+            }
+        }
+    }
+}
+
+// The tile shape of the blocked FGP kernel: 64 x 56 tiles, 8 iterations per launch.
+constexpr int kFgpV = 2, kFgpR = 7, kFgpRW = 8, kFgpTB = 8;
 
 // PDHG dual step: p = Pi(p - s grad ubar), s = sigma / lambda.
 __global__ void __launch_bounds__(kSolverBlockX * kSolverBlockY)
@@ -164,7 +299,7 @@ static tvspec_status check_rof_request(const tvspec_rof_request &q) {
     if (q.H < 1 || q.W < 1 || q.H > 65535 || (size_t)q.H * q.W > ((size_t)1 << 28))
         return fail(TVSPEC_EINVAL, "H, W must be >= 1 with H <= 65535 and H*W <= 2^28");
     if (!std::isfinite(q.lambda) || !(q.lambda > 0.0)) return fail(TVSPEC_EINVAL, "lambda must be > 0");
-    if (q.solver < TVSPEC_SOLVER_CHAMBOLLE || q.solver > TVSPEC_SOLVER_PDHG)
+    if (q.solver < TVSPEC_SOLVER_CHAMBOLLE || q.solver > TVSPEC_SOLVER_FGP_REFERENCE)
         return fail(TVSPEC_EINVAL, "unknown solver");
     if (q.max_iter < 0 || q.max_iter > 10000000) return fail(TVSPEC_EINVAL, "max_iter out of range");
     if (q.check_every < 1) return fail(TVSPEC_EINVAL, "check_every must be >= 1");
@@ -233,7 +368,7 @@ static tvspec_status rof_solve_locked(tvspec_plan *plan, tvspec_rof_request &q, 
         SV_CK(cudaMemcpyAsync(B.u, B.g, pb, cudaMemcpyDeviceToDevice, st));
         SV_CK(cudaMemcpyAsync(B.ub, B.g, pb, cudaMemcpyDeviceToDevice, st));
     }
-    if (q.solver == TVSPEC_SOLVER_FGP) {  // r = p
+    if (q.solver == TVSPEC_SOLVER_FGP || q.solver == TVSPEC_SOLVER_FGP_REFERENCE) {  // r = p
         SV_CK(cudaMemcpyAsync(B.r1[0], B.p1[0], pb, cudaMemcpyDeviceToDevice, st));
         SV_CK(cudaMemcpyAsync(B.r2[0], B.p2[0], pb, cudaMemcpyDeviceToDevice, st));
     }
@@ -279,7 +414,8 @@ static tvspec_status rof_solve_locked(tvspec_plan *plan, tvspec_rof_request &q, 
             tvspec_status s = run_iterations(plan, d, st, &fc);
             if (s != TVSPEC_OK) return finish(s);
             if (fc == 1) cur_p ^= 1;
-        } else if (q.solver == TVSPEC_SOLVER_FGP) {
+        } else if (q.solver == TVSPEC_SOLVER_FGP_REFERENCE) {
+            // one iteration per launch; p in place in copy 0, r ping-pong
             for (int k = 0; k < m; ++k) {
                 const double t_new = (1.0 + std::sqrt(1.0 + 4.0 * t_fgp * t_fgp)) / 2.0;
                 const double beta = (t_fgp - 1.0) / t_new;
@@ -289,6 +425,35 @@ static tvspec_status rof_solve_locked(tvspec_plan *plan, tvspec_rof_request &q, 
                 t_fgp = t_new;
             }
             nk += m;
+        } else if (q.solver == TVSPEC_SOLVER_FGP) {
+            // temporally blocked: up to kFgpTB iterations per launch, p and r ping-pong together
+            constexpr int OW = 32 * kFgpV - 2 * ((kFgpTB + kFgpV - 1) / kFgpV * kFgpV);
+            constexpr int OH = kFgpRW * kFgpR - 2 * kFgpTB;
+            const int ntx = (W + OW - 1) / OW, nty = (H + OH - 1) / OH;
+            FgpDesc fd;
+            fd.gl = B.gl;
+            for (int c = 0; c < 2; ++c) {
+                fd.p1[c] = B.p1[c];
+                fd.p2[c] = B.p2[c];
+                fd.r1[c] = B.r1[c];
+                fd.r2[c] = B.r2[c];
+            }
+            fd.H = H;
+            fd.W = W;
+            fd.pitch = pitch;
+            for (int done = 0; done < m;) {
+                const int n = std::min(kFgpTB, m - done);
+                FgpBetas bt{};
+                for (int k = 0; k < n; ++k) {
+                    const double t_new = (1.0 + std::sqrt(1.0 + 4.0 * t_fgp * t_fgp)) / 2.0;
+                    bt.v[k] = (float)((t_fgp - 1.0) / t_new);
+                    t_fgp = t_new;
+                }
+                k_fgp_tiled<kFgpV, kFgpR, kFgpRW, kFgpTB><<<ntx * nty, 32 * kFgpRW, 0, st>>>(fd, ntx, cur_p, n, bt);
+                cur_p ^= 1;
+                done += n;
+                ++nk;
+            }
         } else {
             for (int k = 0; k < m; ++k) {
                 k_pdhg_dual<<<grid, blk, 0, st>>>(B.p1[0], B.p2[0], B.ub, H, W, pitch,

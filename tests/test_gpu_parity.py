@@ -329,6 +329,34 @@ def test_config3_full_run_properties(plan):
     assert np.array_equal(b["bands"], 2 * a["bands"]) and np.array_equal(b["S"], a["S"])
 
 
+def test_config2_full_batch_as_benchmarked(plan):
+    # the whole config-2 batch (64 images 128..1024 square-ish, K 20..60, three dt) in the
+    # launch configuration the bench times (device memory, one batch): every image
+    # reconstructs, the smallest ones match the oracle in full, and each sampled image is
+    # bit-identical to its decomposition alone
+    import torch
+
+    wl = syn.config2()
+    jobs = [(torch.from_numpy(j.f).cuda(), j.dt, j.K, j.n_inner, j.edges) for j in wl.jobs]
+    outs = plan.decompose_batch(jobs)
+    torch.cuda.synchronize()
+    for j, o in zip(wl.jobs, outs):
+        rec = o["bands"].double().sum(0).cpu().numpy() + o["residual"].cpu().numpy()
+        assert np.abs(rec - j.f).max() <= 1e-5 * np.abs(j.f).max()
+        assert bool(torch.isfinite(o["S"]).all()) and bool((o["S"] >= 0).all())
+    order = sorted(range(len(wl.jobs)), key=lambda i: wl.jobs[i].f.size)
+    for i in order[:2]:
+        j = wl.jobs[i]
+        ref = oracle.decompose(j.f, j.dt, j.K, j.n_inner, j.edges)
+        got = {k: outs[i][k].cpu().numpy() for k in ("bands", "residual", "S")}
+        assert_parity(got, ref, j.f, f"config2 image {i} {j.f.shape}")
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        alone = plan.decompose(*jobs[i])
+        torch.cuda.synchronize()
+        for k in ("bands", "residual", "S"):
+            assert torch.equal(alone[k], outs[i][k]), (i, k)
+
+
 @pytest.mark.parametrize("storage", [1, 2, 3])
 def test_16bit_dual_storage_reports_error(tv, storage):
     # fp16 / bf16 / snorm16 storage of p between launches: errors are reported, no bar is promised;

@@ -106,3 +106,14 @@ def test_invalid_solver_arguments(plan, tv):
             plan.rof_solve(g, 0.5, **args)
         assert ei.value.status == tv.EINVAL
     assert np.isfinite(plan.rof_solve(g, 0.5, "pdhg", max_iter=10)["u"]).all()
+
+
+@pytest.mark.parametrize("H,W,n", [(64, 64, 37), (200, 333, 21), (1, 9, 9), (130, 70, 8), (517, 260, 50)])
+def test_blocked_fgp_matches_the_one_iteration_kernel_bit_for_bit(plan, H, W, n):
+    # register tiles with overlapped halos change where an iteration is computed, not its bits
+    g = _img(H, W, 3 * H + W)
+    a = plan.rof_solve(g, 0.5, "fgp", max_iter=n)
+    b = plan.rof_solve(g, 0.5, "fgp_reference", max_iter=n)
+    for k in ("u", "p1", "p2"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["gap"] == b["gap"]
