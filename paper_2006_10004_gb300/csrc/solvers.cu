@@ -36,10 +36,15 @@ __device__ __forceinline__ void fgp_pixel(float &p1, float &p2, float &r1, float
                                           float G2, float beta) {
     float q1 = __fadd_rn(r1, __fmul_rn(G1, 0.125f));
     float q2 = __fadd_rn(r2, __fmul_rn(G2, 0.125f));
-    const float n = __fsqrt_rn(__fadd_rn(__fmul_rn(q1, q1), __fmul_rn(q2, q2)));
-    if (n > 1.0f) {
-        q1 = __fdiv_rn(q1, n);
-        q2 = __fdiv_rn(q2, n);
+    const float n2 = __fadd_rn(__fmul_rn(q1, q1), __fmul_rn(q2, q2));
+    if (n2 > 1.0f) {
+        // 1/|q| by the hardware reciprocal square root and one Newton-Raphson step,
+        // y <- y (3/2 - n2 y^2 / 2)
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(n2));
+        y = __fmul_rn(y, __fmaf_rn(__fmul_rn(-0.5f, n2), __fmul_rn(y, y), 1.5f));
+        q1 = __fmul_rn(q1, y);
+        q2 = __fmul_rn(q2, y);
     }
     r1 = __fadd_rn(q1, __fmul_rn(beta, __fsub_rn(q1, p1)));
     r2 = __fadd_rn(q2, __fmul_rn(beta, __fsub_rn(q2, p2)));
