@@ -293,7 +293,7 @@ void LaunchSet::release() {
     d_descs = nullptr;
     d_tiles = nullptr;
     d_ep_img = d_ep_base = nullptr;
-    cap_descs = cap_tiles = cap_ep = 0;
+    cap_descs = cap_tiles = cap_ep = cap_base = 0;
 }
 
 void tiles_for(int shape, int H, int W, int *ntx, int *nty) {
@@ -307,11 +307,14 @@ template <typename T>
 static tvspec_status grow_upload(T **dptr, size_t *cap, const std::vector<T> &h) {
     const size_t need = std::max<size_t>(h.size(), 1);
     if (need > *cap) {
+        // cudaFree / cudaMalloc wait for the device: grow geometrically so that a table that
+        // is rebuilt often (the serving loop's) reallocates only a few times
+        const size_t grow = std::max(need, 2 * *cap);
         cudaFree(*dptr);
         *dptr = nullptr;
         *cap = 0;
-        TV_CK(cudaMalloc((void **)dptr, need * sizeof(T)));
-        *cap = need;
+        TV_CK(cudaMalloc((void **)dptr, grow * sizeof(T)));
+        *cap = grow;
     }
     if (!h.empty()) TV_CK(cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     return TVSPEC_OK;
@@ -341,10 +344,7 @@ tvspec_status launchset_build(LaunchSet *ls, const std::vector<ImgDesc> &descs, 
     if ((s = grow_upload(&ls->d_descs, &ls->cap_descs, descs)) != TVSPEC_OK) return s;
     if ((s = grow_upload(&ls->d_tiles, &ls->cap_tiles, tiles)) != TVSPEC_OK) return s;
     if ((s = grow_upload(&ls->d_ep_img, &ls->cap_ep, ep_img)) != TVSPEC_OK) return s;
-    size_t cap_base = 0;
-    cudaFree(ls->d_ep_base);
-    ls->d_ep_base = nullptr;
-    if ((s = grow_upload(&ls->d_ep_base, &cap_base, ep_base)) != TVSPEC_OK) return s;
+    if ((s = grow_upload(&ls->d_ep_base, &ls->cap_base, ep_base)) != TVSPEC_OK) return s;
     ls->n = n;
     ls->shape = shape;
     ls->depth = depth;

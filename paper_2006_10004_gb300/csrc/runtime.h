@@ -76,7 +76,7 @@ struct LaunchSet {
     ImgDesc *d_descs = nullptr;
     TileRef *d_tiles = nullptr;
     int *d_ep_img = nullptr, *d_ep_base = nullptr;
-    size_t cap_descs = 0, cap_tiles = 0, cap_ep = 0;
+    size_t cap_descs = 0, cap_tiles = 0, cap_ep = 0, cap_base = 0;
     std::vector<ImgDesc> h_descs;
     std::vector<int> tile_prefix, ep_prefix;
     void release();
