@@ -1127,6 +1127,8 @@ tvspec_status tvspec_plan_destroy(tvspec_plan *plan) {
     tvspec_server_stop(plan);
     cudaSetDevice(plan->device);
     cudaStreamSynchronize(plan->stream);
+    if (plan->h_word) cudaFreeHost(plan->h_word);
+    plan->h_word = nullptr;
     for (auto &E : plan->cache) free_entry(*E, plan->stream);
     plan->cache.clear();
     for (auto &kv : plan->iter_sets) kv.second->release();

@@ -117,6 +117,7 @@ struct tvspec_plan {
     std::list<std::unique_ptr<tvspec::CacheEntry>> cache;  // most recent first
     std::map<std::string, std::pair<int, int>> tune;         // key -> (shape, depth)
     std::string tune_cache;   // file keeping tune across processes ("" = none)
+    double *h_word = nullptr; // page-locked scalar for small device-to-host reads (plan->mu held)
     std::string tune_prefix;  // this GPU model and shape table, first field of the file lines
     std::map<std::string, std::unique_ptr<tvspec::LaunchSet>> iter_sets;
     std::list<tvspec::Slot> scratch;                        // buffers of tvspec_rof_step etc.

@@ -341,11 +341,9 @@ static tvspec_status rof_solve_locked(tvspec_plan *plan, tvspec_rof_request &q, 
     B.partials = reinterpret_cast<double *>(base + pa * 12);
     B.gap = reinterpret_cast<double *>(base + pa * 12 + (((size_t)gap_blocks * 8 + 255) & ~(size_t)255));
     B.words = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(B.gap) + 128);
-    double *h_gap = nullptr;
     auto finish = [&](tvspec_status s) {
         cudaFreeAsync(base, st);
         cudaStreamSynchronize(st);
-        if (h_gap) cudaFreeHost(h_gap);
         return s;
     };
 #define SV_CK(call)                                                   \
@@ -353,7 +351,8 @@ static tvspec_status rof_solve_locked(tvspec_plan *plan, tvspec_rof_request &q, 
         cudaError_t e_ = (call);                                      \
         if (e_ != cudaSuccess) return finish(fail_cuda(e_, #call));   \
     } while (0)
-    SV_CK(cudaMallocHost((void **)&h_gap, sizeof(double)));
+    if (!plan->h_word) SV_CK(cudaMallocHost((void **)&plan->h_word, sizeof(double)));
+    double *h_gap = plan->h_word;
     SV_CK(cudaMemsetAsync(base, 0, total, st));  // zero padding columns, p, r, words
     const cudaMemcpyKind in_kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind out_kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
