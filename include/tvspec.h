@@ -77,7 +77,9 @@ typedef struct {
     int fast_math;          /* 1 (default): hardware approximate sqrt/reciprocal; 0: IEEE-rounded */
     size_t mem_budget_bytes;/* device memory the serving scheduler may hold; 0 = 60 GiB */
     int max_batch;          /* serving: most requests resident at once; 0 = 256 */
-    int pdl;                /* 1: programmatic dependent launch between the kernels of a step; default 0 */
+    int pdl;                /* 1 (default): programmatic dependent launch between the kernels of a
+                               step (the next kernel is scheduled while the previous one drains;
+                               each waits for its predecessor's results before reading them); 0 off */
     int persistent;         /* 1: run a single image's step in one cooperative launch (tiles
                                resident for the whole step, bounded-wait grid barriers) when all
                                its tiles fit on the GPU at once; 0 (default): one launch per block

@@ -1069,7 +1069,7 @@ void tvspec_config_init(tvspec_config *cfg) {
     cfg->fast_math = 1;
     cfg->mem_budget_bytes = 0;
     cfg->max_batch = 0;
-    cfg->pdl = 0;
+    cfg->pdl = 1;
     cfg->persistent = 0;
     cfg->barrier_timeout_ms = 2000;
     cfg->test_barrier_noshow = -1;
