@@ -104,31 +104,11 @@ cudaError_t launch_init(const ImgDesc *descs, const int *ep_img, const int *ep_b
 //   S(t_k)  = sum |phi_k|                     (deterministic two-level reduction)
 //   b^m    += phi_k dt for the band m of t_k; a finished band is written out as float32
 //   f_r     = u_{K-1} - t_{K-1} (u_K - u_{K-1}) / dt at the last step (Eq. finite_inverse_trafo)
-template <typename P>
-__device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gstep, int depth,
-                                               double *s_red, int &s_last) {
+// S(t_k) (and the Parseval-type spectrum) of one epilogue block's values: a fixed-order block
+// tree into the block's partial, and in the image's last block the partials in block order.
+__device__ __forceinline__ void s_reduce(const ImgDesc &dd, int lb, int k, double absphi,
+                                         double phif, double *s_red, int &s_last) {
     const ImgDesc *d = &dd;
-    const int k = gstep - d->s0;
-    if (k < 0 || k >= d->K) return;  // uniform over the block
-    const int H = d->H, W = d->W, pitch = d->pitch;
-    const int nbx = (W + kEpBlock - 1) / kEpBlock;
-    const int i = lb / nbx;
-    const int j = (lb % nbx) * kEpBlock + threadIdx.x;
-    double absphi = 0.0, phif = 0.0;
-    if (j < W) {
-        // the copy of p written by the step's last launch
-        const int cp = p_copy(k + 1, launches_per_step(d->n_inner, depth), 0);
-        const P *p1 = static_cast<const P *>(d->p1[cp]);
-        const P *p2 = static_cast<const P *>(d->p2[cp]);
-        const size_t o = (size_t)i * pitch + j;
-        const DivTerms dv =
-            div_terms(i, j, H, W, PStore<P>::load(p1[o]), i > 0 ? PStore<P>::load(p1[o - pitch]) : 0.0f,
-                      PStore<P>::load(p2[o]), j > 0 ? PStore<P>::load(p2[o - 1]) : 0.0f);
-        float gl_next;
-        absphi = epilogue_pixel(*d, k, (size_t)i * W + j, dv, &gl_next, &phif);
-        d->gl[o] = gl_next;
-    }
-    if (k < 1) return;  // no phi at step 0
     const double bsum = block_sum(absphi, s_red);
     const double psum = d->S_par ? block_sum(phif, s_red) : 0.0;  // uniform per image
     if (threadIdx.x == 0) {
@@ -158,6 +138,117 @@ __device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gs
         if (d->S_par) d->S_par[k - 1] = ptot;
         *d->counter = 0u;
     }
+}
+
+// The divergence terms at pixel (i, j) from the copy of p the step's last launch wrote.
+template <typename P>
+__device__ __forceinline__ DivTerms step_div_terms(const ImgDesc &d, int k, int i, int j, int depth) {
+    const int cp = p_copy(k + 1, launches_per_step(d.n_inner, depth), 0);
+    const P *p1 = static_cast<const P *>(d.p1[cp]);
+    const P *p2 = static_cast<const P *>(d.p2[cp]);
+    const size_t o = (size_t)i * d.pitch + j;
+    return div_terms(i, j, d.H, d.W, PStore<P>::load(p1[o]), i > 0 ? PStore<P>::load(p1[o - d.pitch]) : 0.0f,
+                     PStore<P>::load(p2[o]), j > 0 ? PStore<P>::load(p2[o - 1]) : 0.0f);
+}
+
+template <typename P>
+__device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gstep, int depth,
+                                               double *s_red, int &s_last) {
+    const ImgDesc *d = &dd;
+    const int k = gstep - d->s0;
+    if (k < 0 || k >= d->K) return;  // uniform over the block
+    const int W = d->W;
+    const int nbx = (W + kEpBlock - 1) / kEpBlock;
+    const int i = lb / nbx;
+    const int j = (lb % nbx) * kEpBlock + threadIdx.x;
+    double absphi = 0.0, phif = 0.0;
+    if (j < W) {
+        const DivTerms dv = step_div_terms<P>(*d, k, i, j, depth);
+        float gl_next;
+        absphi = epilogue_pixel(*d, k, (size_t)i * W + j, dv, &gl_next, &phif);
+        d->gl[(size_t)i * d->pitch + j] = gl_next;
+    }
+    if (k < 1) return;  // no phi at step 0
+    s_reduce(*d, lb, k, absphi, phif, s_red, s_last);
+}
+
+// Split epilogue (u in the three-buffer rotation, u_k in u_buf3(k)). First part: u_{k+1} and
+// g/dt of the next step; it is all the next step's dual iterations need.
+template <typename P>
+__device__ __forceinline__ void epi_primal_block(const ImgDesc &d, int lb, int gstep, int depth) {
+    const int k = gstep - d.s0;
+    if (k < 0 || k >= d.K) return;
+    const int W = d.W;
+    const int nbx = (W + kEpBlock - 1) / kEpBlock;
+    const int i = lb / nbx;
+    const int j = (lb % nbx) * kEpBlock + threadIdx.x;
+    if (j >= W) return;
+    const size_t n = (size_t)i * W + j;
+    const DivTerms dv = step_div_terms<P>(d, k, i, j, depth);
+    float gl_next;
+    if (d.acc_mode) {
+        const ff un = epi_primal<FFOps>(d, k, n, dv, FFOps::load(u_buf3(d, k), n), &gl_next);
+        FFOps::store(u_buf3(d, k + 1), n, un);
+    } else {
+        const double un = epi_primal<F64Ops>(d, k, n, dv, F64Ops::load(u_buf3(d, k), n), &gl_next);
+        F64Ops::store(u_buf3(d, k + 1), n, un);
+    }
+    d.gl[(size_t)i * d.pitch + j] = gl_next;
+}
+
+// Second part (k >= 1): phi_k, S, bands, filters and residual from u_{k-1}, u_k, u_{k+1}. It runs
+// beside the next step's dual iterations, which do not read any of it.
+__device__ __forceinline__ void epi_spectral_block(const ImgDesc &d, int lb, int gstep,
+                                                   double *s_red, int &s_last) {
+    const int k = gstep - d.s0;
+    if (k < 1 || k >= d.K) return;  // uniform over the block
+    const int W = d.W;
+    const int nbx = (W + kEpBlock - 1) / kEpBlock;
+    const int i = lb / nbx;
+    const int j = (lb % nbx) * kEpBlock + threadIdx.x;
+    double absphi = 0.0, phif = 0.0;
+    if (j < W) {
+        const size_t n = (size_t)i * W + j;
+        const double *bp = u_buf3(d, k - 1), *bc = u_buf3(d, k), *bn = u_buf3(d, k + 1);
+        absphi = d.acc_mode
+                     ? epi_spectral<FFOps>(d, k, n, FFOps::load(bp, n), FFOps::load(bc, n), FFOps::load(bn, n), &phif)
+                     : epi_spectral<F64Ops>(d, k, n, F64Ops::load(bp, n), F64Ops::load(bc, n), F64Ops::load(bn, n), &phif);
+    }
+    s_reduce(d, lb, k, absphi, phif, s_red, s_last);
+}
+
+template <typename P>
+__global__ void __launch_bounds__(kEpBlock)
+    k_epi_primal(const ImgDesc *__restrict__ descs, const int *__restrict__ ep_img,
+                 const int *__restrict__ ep_base, int gstep, int depth) {
+    pdl_wait();
+    pdl_trigger();
+    const int img = ep_img[blockIdx.x];
+    epi_primal_block<P>(descs[img], blockIdx.x - ep_base[img], gstep, depth);
+}
+
+template <typename P>
+__global__ void __launch_bounds__(kEpBlock)
+    k_epi_primal_one(const __grid_constant__ ImgDesc d, int gstep, int depth) {
+    pdl_wait();
+    pdl_trigger();
+    epi_primal_block<P>(d, blockIdx.x, gstep, depth);
+}
+
+__global__ void __launch_bounds__(kEpBlock)
+    k_epi_spectral(const ImgDesc *__restrict__ descs, const int *__restrict__ ep_img,
+                   const int *__restrict__ ep_base, int gstep) {
+    __shared__ double s_red[kEpBlock / 32];
+    __shared__ int s_last;
+    const int img = ep_img[blockIdx.x];
+    epi_spectral_block(descs[img], blockIdx.x - ep_base[img], gstep, s_red, s_last);
+}
+
+__global__ void __launch_bounds__(kEpBlock)
+    k_epi_spectral_one(const __grid_constant__ ImgDesc d, int gstep) {
+    __shared__ double s_red[kEpBlock / 32];
+    __shared__ int s_last;
+    epi_spectral_block(d, blockIdx.x, gstep, s_red, s_last);
 }
 
 template <typename P>
@@ -226,6 +317,63 @@ cudaError_t launch_epilogue_one(int p_storage, const ImgDesc &d, int gstep, int 
         case 3: return cudaLaunchKernelEx(&cfg, k_epilogue_one<short>, d, gstep, depth);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_epi_primal(int p_storage, const ImgDesc *descs, const int *ep_img,
+                              const int *ep_base, int n_blocks, int gstep, int depth,
+                              cudaStream_t st, bool pdl) {
+    if (n_blocks <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_blocks);
+    cfg.blockDim = dim3(kEpBlock);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    switch (p_storage) {
+        case 0: return cudaLaunchKernelEx(&cfg, k_epi_primal<float>, descs, ep_img, ep_base, gstep, depth);
+        case 1: return cudaLaunchKernelEx(&cfg, k_epi_primal<__half>, descs, ep_img, ep_base, gstep, depth);
+        case 2: return cudaLaunchKernelEx(&cfg, k_epi_primal<__nv_bfloat16>, descs, ep_img, ep_base, gstep, depth);
+        case 3: return cudaLaunchKernelEx(&cfg, k_epi_primal<short>, descs, ep_img, ep_base, gstep, depth);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_epi_primal_one(int p_storage, const ImgDesc &d, int gstep, int depth,
+                                  cudaStream_t st, bool pdl) {
+    const int n_blocks = d.ep_blocks;
+    if (n_blocks <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_blocks);
+    cfg.blockDim = dim3(kEpBlock);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    switch (p_storage) {
+        case 0: return cudaLaunchKernelEx(&cfg, k_epi_primal_one<float>, d, gstep, depth);
+        case 1: return cudaLaunchKernelEx(&cfg, k_epi_primal_one<__half>, d, gstep, depth);
+        case 2: return cudaLaunchKernelEx(&cfg, k_epi_primal_one<__nv_bfloat16>, d, gstep, depth);
+        case 3: return cudaLaunchKernelEx(&cfg, k_epi_primal_one<short>, d, gstep, depth);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_epi_spectral(const ImgDesc *descs, const int *ep_img, const int *ep_base,
+                                int n_blocks, int gstep, cudaStream_t st) {
+    if (n_blocks <= 0) return cudaSuccess;
+    k_epi_spectral<<<n_blocks, kEpBlock, 0, st>>>(descs, ep_img, ep_base, gstep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_epi_spectral_one(const ImgDesc &d, int gstep, cudaStream_t st) {
+    if (d.ep_blocks <= 0) return cudaSuccess;
+    k_epi_spectral_one<<<d.ep_blocks, kEpBlock, 0, st>>>(d, gstep);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------

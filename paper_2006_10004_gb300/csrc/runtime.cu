@@ -104,7 +104,7 @@ tvspec_status make_job(const tvspec_request &req, Job *out) {
 // ---------------------------------------------------------------------------------------------
 struct SlotLayout {
     size_t band, fH, fres, f, p1, p2, q1, q2, gl, acc, facc, filt, bands, partials, ctr, ua, ub,
-        res, S, tr, spar, ppar, zero_begin, zero_end, total;
+        u3, res, S, tr, spar, ppar, zero_begin, zero_end, total;
 };
 
 static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naive, bool trace,
@@ -138,6 +138,7 @@ static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naiv
     L.filt = take((size_t)nf * N * 4);
     L.ua = take(N * 8);
     L.ub = take(N * 8);
+    L.u3 = take(N * 8);
     L.res = take(N * 4);
     L.S = take((size_t)std::max(K - 1, 1) * 8);
     L.tr = trace ? take((size_t)(K + 1) * N * 8) : 0;
@@ -197,6 +198,7 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
     x.status = x.counter + 1;
     x.ua = (double *)(base + L.ua);
     x.ub = (double *)(base + L.ub);
+    x.u3 = (double *)(base + L.u3);
     x.residual = (float *)(base + L.res);
     x.S = (double *)(base + L.S);
     x.utrace = trace ? (double *)(base + L.tr) : nullptr;
@@ -241,6 +243,7 @@ ImgDesc slot_desc(const Slot &s, int s0) {
     d.gl = s.gl;
     d.ua = s.ua;
     d.ub = s.ub;
+    d.u3 = s.u3;
     d.acc = s.acc;
     d.bands = s.bands;
     d.residual = s.residual;
@@ -630,6 +633,47 @@ tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *>
     return TVSPEC_OK;
 }
 
+// One ROF step with the split epilogue: cold-start clears, the dual iterations, then (after the
+// previous step's spectral part, whose u_{k-2} buffer this step's primal part overwrites) the
+// primal part on `st`, and the spectral part forked onto the plan's side stream.
+static tvspec_status enqueue_step_split(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *> &slots,
+                                        int n_active, int gstep, cudaStream_t st, bool *pending,
+                                        uint64_t *nk) {
+    const tvspec_config &c = plan->cfg;
+    if (!c.warm_start) {
+        for (int i = 0; i < n_active; ++i) {
+            const int k = gstep - ls.h_descs[i].s0;
+            if (k < 0 || k >= slots[i]->K) continue;
+            for (int cpy = 0; cpy < 2; ++cpy) {
+                TV_CK(cudaMemsetAsync(slots[i]->p1[cpy], 0, slots[i]->p_bytes, st));
+                TV_CK(cudaMemsetAsync(slots[i]->p2[cpy], 0, slots[i]->p_bytes, st));
+            }
+        }
+    }
+    tvspec_status s = enqueue_iterations(plan, ls, slots, n_active, gstep, st, nk);
+    if (s != TVSPEC_OK) return s;
+    if (*pending) TV_CK(cudaStreamWaitEvent(st, plan->ev_join, 0));
+    const int ep_depth = ls.shape < 0 ? 1 : ls.depth;
+    const bool one = ls.n == 1 && n_active == 1;
+    const int nblk = ls.ep_prefix[n_active];
+    cudaError_t e = one ? launch_epi_primal_one(c.p_storage, ls.h_descs[0], gstep, ep_depth, st, c.pdl != 0)
+                        : launch_epi_primal(c.p_storage, ls.d_descs, ls.d_ep_img, ls.d_ep_base, nblk,
+                                            gstep, ep_depth, st, c.pdl != 0);
+    if (e != cudaSuccess) return fail_cuda(e, "epilogue launch");
+    if (nblk > 0) ++*nk;
+    if (gstep >= 1 && nblk > 0) {  // phi from the second step on (every image here has s0 = 0)
+        TV_CK(cudaEventRecord(plan->ev_fork, st));
+        TV_CK(cudaStreamWaitEvent(plan->side, plan->ev_fork, 0));
+        e = one ? launch_epi_spectral_one(ls.h_descs[0], gstep, plan->side)
+                : launch_epi_spectral(ls.d_descs, ls.d_ep_img, ls.d_ep_base, nblk, gstep, plan->side);
+        if (e != cudaSuccess) return fail_cuda(e, "epilogue launch");
+        TV_CK(cudaEventRecord(plan->ev_join, plan->side));
+        *pending = true;
+        ++*nk;
+    }
+    return TVSPEC_OK;
+}
+
 // The whole decomposition of a cached batch, from cleared workspace to the last epilogue.
 static tvspec_status enqueue_decomposition(tvspec_plan *plan, CacheEntry &E, cudaStream_t st,
                                            uint64_t *nk) {
@@ -651,17 +695,24 @@ static tvspec_status enqueue_decomposition(tvspec_plan *plan, CacheEntry &E, cud
         off += g.second;
     }
     if (E.n_tiled == 0) return TVSPEC_OK;
+    const bool split = true;  // the split epilogue (the serving loop uses the combined one)
     cudaError_t e = launch_init(E.ls.d_descs, E.ls.d_ep_img, E.ls.d_ep_base,
                                 E.ls.ep_prefix[E.n_tiled], st);
     if (e != cudaSuccess) return fail_cuda(e, "init launch");
     ++*nk;
+    bool pending = false;  // a spectral part on the side stream not yet joined
     for (int g = 0; g < E.maxK; ++g) {
         int n_active = 0;
         while (n_active < E.n_tiled && E.slots[n_active].K > g) ++n_active;
         if (n_active == 0) break;
-        tvspec_status s = enqueue_step(plan, E.ls, sp, n_active, g, st, nk);
-        if (s != TVSPEC_OK) return s;
+        tvspec_status s = split ? enqueue_step_split(plan, E.ls, sp, n_active, g, st, &pending, nk)
+                                : enqueue_step(plan, E.ls, sp, n_active, g, st, nk);
+        if (s != TVSPEC_OK) {
+            if (pending) cudaStreamWaitEvent(st, plan->ev_join, 0);  // rejoin before returning
+            return s;
+        }
     }
+    if (pending) TV_CK(cudaStreamWaitEvent(st, plan->ev_join, 0));
     return TVSPEC_OK;
 }
 
@@ -1111,7 +1162,13 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
     p->tune_prefix = tune_prefix_for(device);
     tune_cache_load(p);
     e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+        if (p->side) cudaStreamDestroy(p->side);
+        if (p->stream) cudaStreamDestroy(p->stream);
         delete p;
         return fail_cuda(e, "stream creation");
     }
@@ -1138,6 +1195,10 @@ tvspec_status tvspec_plan_destroy(tvspec_plan *plan) {
     cudaFree(plan->ping);
     plan->ping = nullptr;
     cudaStreamSynchronize(plan->stream);
+    cudaStreamSynchronize(plan->side);
+    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    cudaStreamDestroy(plan->side);
     cudaStreamDestroy(plan->stream);
     delete plan;
     return TVSPEC_OK;

@@ -49,7 +49,7 @@ struct Slot {
     float *f = nullptr;
     void *p1[2] = {nullptr, nullptr}, *p2[2] = {nullptr, nullptr};  // two copies of p
     float *gl = nullptr;
-    double *ua = nullptr, *ub = nullptr, *acc = nullptr;
+    double *ua = nullptr, *ub = nullptr, *u3 = nullptr, *acc = nullptr;
     float *bands = nullptr, *residual = nullptr;
     double *S = nullptr, *utrace = nullptr, *partials = nullptr;
     unsigned *counter = nullptr, *status = nullptr;
@@ -113,6 +113,10 @@ struct tvspec_plan {
     int device = 0;
     tvspec_config cfg{};
     cudaStream_t stream = nullptr;
+    // second stream and events of the split epilogue: the spectral part of step k runs on
+    // `side` beside step k+1's dual iterations on the main stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::mutex mu;  // serialises the plain and batched paths
     std::list<std::unique_ptr<tvspec::CacheEntry>> cache;  // most recent first
     std::map<std::string, std::pair<int, int>> tune;         // key -> (shape, depth)

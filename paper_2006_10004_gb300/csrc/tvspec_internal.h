@@ -26,6 +26,7 @@ struct ImgDesc {
     void *p1[2], *p2[2];
     float *gl;              // g / lambda of the current ROF step, float32, pitched
     double *ua, *ub;        // u ping-pong (compact H*W): u_k is ua for even k, ub for odd k
+    double *u3;             // third u buffer of the split epilogue: u_k in {ua, ub, u3}[k % 3]
     double *acc;            // running sum of the active band (compact H*W)
     float *bands;           // (n_bands) H W output (compact), device
     float *residual;        // H W output (compact), device
@@ -167,6 +168,19 @@ cudaError_t launch_epilogue(int p_storage, const ImgDesc *descs, const int *ep_i
 // The epilogue of one image whose descriptor is passed by value (block b = local block b).
 cudaError_t launch_epilogue_one(int p_storage, const ImgDesc &d, int gstep, int depth,
                                 cudaStream_t st, bool pdl = false);
+
+// The epilogue split in two (u in the three-buffer rotation ua / ub / u3, u_k in [k % 3]):
+// the primal part (u_{k+1}, g/dt: all the next step's iterations need) and the spectral part
+// (phi_k, S, bands, filters, residual), which may run beside the next step's iterations. The
+// same per-pixel operations as the combined epilogue, so the same bits.
+cudaError_t launch_epi_primal(int p_storage, const ImgDesc *descs, const int *ep_img,
+                              const int *ep_base, int n_blocks, int gstep, int depth,
+                              cudaStream_t st, bool pdl = false);
+cudaError_t launch_epi_primal_one(int p_storage, const ImgDesc &d, int gstep, int depth,
+                                  cudaStream_t st, bool pdl = false);
+cudaError_t launch_epi_spectral(const ImgDesc *descs, const int *ep_img, const int *ep_base,
+                                int n_blocks, int gstep, cudaStream_t st);
+cudaError_t launch_epi_spectral_one(const ImgDesc &d, int gstep, cudaStream_t st);
 
 // One ROF step's primal recovery for the standalone ROF entry: u = g - lambda div p (float32
 // inputs, float32 output, compact layout for u and g, pitched p).
