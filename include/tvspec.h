@@ -73,7 +73,8 @@ typedef struct {
     int kernel;             /* TVSPEC_KERNEL_*; default TVSPEC_KERNEL_AUTO */
     int tile;               /* tile-shape index (see tvspec_tile_info), -1 = autotune; default -1 */
     int temporal_block;     /* dual iterations per tiled launch (1..16), 0 = autotune; default 0 */
-    int use_graphs;         /* 1 (default): replay one CUDA graph per repeated problem shape */
+    int use_graphs;         /* 1 (default): a problem signature used a second time is captured into
+                               a CUDA graph then and replayed from then on (plan-level LRU of 4) */
     int fast_math;          /* 1 (default): hardware approximate sqrt/reciprocal; 0: IEEE-rounded */
     size_t mem_budget_bytes;/* device memory the serving scheduler may hold; 0 = 60 GiB */
     int max_batch;          /* serving: most requests resident at once; 0 = 256 */

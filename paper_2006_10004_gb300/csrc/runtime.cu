@@ -839,26 +839,6 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
         free_entry(*E, plan->stream);
         return fail(TVSPEC_ENOMEM, "pinned status words");
     }
-    if (plan->cfg.use_graphs) {
-        uint64_t nk = 0;
-        TV_CK(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
-        st = enqueue_decomposition(plan, *E, plan->stream, &nk);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(plan->stream, &g);
-        if (st != TVSPEC_OK || e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            free_entry(*E, plan->stream);
-            return st != TVSPEC_OK ? st : fail_cuda(e, "graph capture");
-        }
-        E->graph = g;
-        e = cudaGraphInstantiate(&E->exec, g, 0);
-        if (e != cudaSuccess) {
-            free_entry(*E, plan->stream);
-            return fail_cuda(e, "graph instantiation");
-        }
-        E->graph_kernels = nk;
-        plan->graphs_built++;
-    }
     plan->last_tile = shape;
     plan->last_depth = depth;
     plan->cache.push_front(std::move(E));
@@ -895,7 +875,38 @@ tvspec_status enqueue_copy_list(const std::vector<CopyItem> &items, cudaStream_t
     return TVSPEC_OK;
 }
 
+// Captures the entry's whole decomposition into a CUDA graph (on the plan stream).
+static tvspec_status capture_entry(tvspec_plan *plan, CacheEntry &E) {
+    uint64_t nk = 0;
+    TV_CK(cudaStreamBeginCapture(plan->stream, cudaStreamCaptureModeThreadLocal));
+    tvspec_status st = enqueue_decomposition(plan, E, plan->stream, &nk);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(plan->stream, &g);
+    if (st != TVSPEC_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return st != TVSPEC_OK ? st : fail_cuda(e, "graph capture");
+    }
+    e = cudaGraphInstantiate(&E.exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        E.exec = nullptr;
+        return fail_cuda(e, "graph instantiation");
+    }
+    E.graph = g;
+    E.graph_kernels = nk;
+    plan->graphs_built++;
+    return TVSPEC_OK;
+}
+
 tvspec_status launch_entry(tvspec_plan *plan, CacheEntry &E, cudaStream_t st) {
+    // a problem signature is captured into a graph on its second use: a one-off image (a batch
+    // of many different sizes decomposed one at a time) does not pay for a capture it never
+    // replays
+    if (plan->cfg.use_graphs && !E.exec && E.uses >= 1) {
+        tvspec_status s = capture_entry(plan, E);
+        if (s != TVSPEC_OK) return s;
+    }
+    ++E.uses;
     uint64_t nk = 0;
     if (E.exec) {
         TV_CK(cudaGraphLaunch(E.exec, st));

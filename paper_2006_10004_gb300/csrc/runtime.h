@@ -99,6 +99,7 @@ struct CacheEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t graph_kernels = 0;
+    int uses = 0;                  // decompositions run from this entry (captured on the 2nd)
     unsigned *h_status = nullptr;  // pinned, one word per image
 };
 

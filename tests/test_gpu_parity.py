@@ -125,12 +125,15 @@ def test_graph_and_plain_launches_bit_identical(tv):
     f = _img(90, 77, 8)
     args = (f, 0.5, 5, 31, syn.DYADIC_EDGES)
     with tv.Plan(0, use_graphs=1) as a, tv.Plan(0, use_graphs=0) as b:
-        ra = a.decompose(*args, trace=True)
-        ra2 = a.decompose(*args, trace=True)  # graph replay
+        ra = a.decompose(*args, trace=True)   # first use: launched directly
+        ra2 = a.decompose(*args, trace=True)  # second use: captured into a graph and replayed
+        ra3 = a.decompose(*args, trace=True)  # replay
         rb = b.decompose(*args, trace=True)
-        assert a.stats()["graph_launches"] == 2 and b.stats()["graph_launches"] == 0
+        assert a.stats()["graph_launches"] == 2 and a.stats()["graphs_built"] == 1
+        assert b.stats()["graph_launches"] == 0
     _same(ra, rb)
     _same(ra, ra2)
+    _same(ra, ra3)
 
 
 def test_programmatic_dependent_launch_bit_identical(tv):
