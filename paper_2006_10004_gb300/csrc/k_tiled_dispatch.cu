@@ -23,19 +23,44 @@ void tiled_output_tile(const TileShape &s, int *ow, int *oh) {
     *oh = s.RW * s.R - 2 * s.TB;
 }
 
+static TiledKernel table_kernel(int shape, int p_storage, bool fast) {
+    switch (p_storage) {
+        case 0: return tiled_kernel_f32(shape, fast);
+        case 1: return tiled_kernel_f16(shape, fast);
+        case 2: return tiled_kernel_bf16(shape, fast);
+        case 3: return tiled_kernel_s16(shape, fast);
+        default: return nullptr;
+    }
+}
+
+int tiled_ctas_per_sm(int shape, int p_storage, bool fast, bool one) {
+    constexpr int kMaxShapes = 64;
+    static int cache[kMaxShapes][4][2][2];  // 0 = not asked yet
+    if (shape < 0 || shape >= tiled_shape_count() || shape >= kMaxShapes || p_storage < 0 ||
+        p_storage > 3)
+        return 1;
+    int &c = cache[shape][p_storage][fast ? 1 : 0][one ? 1 : 0];
+    if (c == 0) {
+        int n = 0;
+        const int threads = 32 * kShapes[shape].RW;
+        cudaError_t e = (one && p_storage == 0)
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tiled_one_kernel_f32(shape, fast), threads, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, table_kernel(shape, p_storage, fast), threads, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            n = 1;
+        }
+        c = n > 0 ? n : 1;
+    }
+    return c;
+}
+
 cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *tiles, int n_tiles,
                          const ImgDesc *descs, int gstep, int blk, int depth, float tau,
                          cudaStream_t st, bool pdl) {
     if (shape < 0 || shape >= tiled_shape_count()) return cudaErrorInvalidValue;
     if (n_tiles <= 0) return cudaSuccess;
-    TiledKernel k = nullptr;
-    switch (p_storage) {
-        case 0: k = tiled_kernel_f32(shape, fast); break;
-        case 1: k = tiled_kernel_f16(shape, fast); break;
-        case 2: k = tiled_kernel_bf16(shape, fast); break;
-        case 3: k = tiled_kernel_s16(shape, fast); break;
-        default: return cudaErrorInvalidValue;
-    }
+    TiledKernel k = table_kernel(shape, p_storage, fast);
     if (!k) return cudaErrorInvalidValue;
     const int threads = 32 * kShapes[shape].RW;
     cudaLaunchConfig_t cfg = {};

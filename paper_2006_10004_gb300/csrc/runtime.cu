@@ -368,7 +368,7 @@ static int default_depth(const tvspec_config &c, int shape) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Tune cache file: lines "<prefix> <key> <shape> <depth>", prefix = GPU model, SM count and a
+// Tune cache file: lines "<prefix> <key> <shape> <depth> <pdl>", prefix = GPU model, SM count and a
 // checksum of the tile-shape table, so that choices of another GPU or build are skipped.
 // ---------------------------------------------------------------------------------------------
 static std::string tune_prefix_for(int device) {
@@ -404,68 +404,102 @@ static void tune_cache_load(tvspec_plan *plan) {
     while (std::fgets(line, sizeof(line), fp)) {
         std::istringstream in(line);
         std::string prefix, key;
-        int shape = -1, depth = 0;
+        int shape = -1, depth = 0, pdl = 0;
         if (!(in >> prefix >> key >> shape >> depth)) continue;
+        if (!(in >> pdl)) pdl = 0;
         if (prefix != plan->tune_prefix) continue;
         if (shape < 0 || shape >= tiled_shape_count() || depth < 1 || depth > tiled_shape(shape).TB)
             continue;
-        plan->tune[key] = {shape, depth};
+        plan->tune[key] = {shape, depth, pdl != 0};
     }
     std::fclose(fp);
 }
 
-static void tune_cache_append(tvspec_plan *plan, const std::string &key, int shape, int depth) {
+static void tune_cache_append(tvspec_plan *plan, const std::string &key, int shape, int depth,
+                              bool pdl) {
     if (plan->tune_cache.empty() || key.size() > 3500) return;  // lines stay below 4 KB
     static std::mutex file_mu;  // plans of one process append whole lines
     std::lock_guard<std::mutex> lk(file_mu);
     FILE *fp = std::fopen(plan->tune_cache.c_str(), "a");
     if (!fp) return;  // the cache is an optimisation: an unwritable file is not an error
-    std::fprintf(fp, "%s %s %d %d\n", plan->tune_prefix.c_str(), key.c_str(), shape, depth);
+    std::fprintf(fp, "%s %s %d %d %d\n", plan->tune_prefix.c_str(), key.c_str(), shape, depth,
+                 pdl ? 1 : 0);
     std::fclose(fp);
 }
 
 tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, cudaStream_t st,
-                           int *shape, int *depth, bool table_form) {
+                           int *shape, int *depth, bool table_form, bool *pdl_out) {
     const tvspec_config &c = plan->cfg;
+    bool pdl_dummy = false;
+    bool *pdl = pdl_out ? pdl_out : &pdl_dummy;
+    *pdl = false;
     if (c.kernel == TVSPEC_KERNEL_NAIVE) {
         *shape = -1;
         *depth = 1;
         return TVSPEC_OK;
     }
-    std::vector<int> cands;
+    std::vector<int> shapes;
     if (c.tile >= 0) {
-        cands.push_back(c.tile);
+        shapes.push_back(c.tile);
     } else {
         for (int s = 0; s < tiled_shape_count(); ++s) {
             if (c.p_storage != TVSPEC_P_FP32 && c.temporal_block == 0 && tiled_shape(s).TB < 8)
                 continue;
-            cands.push_back(s);
+            shapes.push_back(s);
         }
-    }
-    if (cands.size() == 1) {
-        *shape = cands[0];
-        *depth = default_depth(c, cands[0]);
-        return TVSPEC_OK;
     }
     // time the form the run will launch: the descriptor-in-parameters kernel for one image,
     // the tile-table kernel for a batch (and for serving, which always uses tables)
     const bool one = !table_form && slots.size() == 1 && tiled_one_available(c.p_storage);
+    // Programmatic dependent launch, measured on whole decompositions: it pays where the tiled
+    // kernel runs one CTA per SM (512^2, tile 24: 12.3 vs 13.0 ms) or its grid spans more than
+    // one wave (1024^2 and 2048^2, tile 26: -4 % / -1 %), and costs up to 40 % where a shape with
+    // room for a second CTA per SM runs a grid below one wave (512^2, tile 26: 17.7 vs 13.0 ms),
+    // the next grid's CTAs then settling beside the running ones. Timing short graphs of
+    // iteration launches alone did not reproduce either effect, so it is a rule, not a timing.
+    auto pdl_rule = [&](int sh) {
+        if (!c.pdl || sh < 0) return false;
+        const int per_sm = tiled_ctas_per_sm(sh, c.p_storage, c.fast_math != 0, one);
+        int n_tiles = 0;
+        for (Slot *s : slots) {
+            int ntx, nty;
+            tiles_for(sh, s->H, s->W, &ntx, &nty);
+            n_tiles += ntx * nty;
+        }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 1;
+        }
+        return per_sm == 1 || n_tiles > per_sm * sms;
+    };
+    std::vector<std::pair<int, bool>> cands;
+    for (int sh : shapes) cands.push_back({sh, false});
+    if (cands.size() == 1 || slots.empty()) {
+        *shape = cands[0].first;
+        *depth = default_depth(c, cands[0].first);
+        *pdl = slots.empty() ? c.pdl != 0 : pdl_rule(*shape);
+        return TVSPEC_OK;
+    }
     std::vector<std::pair<int, int>> dims;
     for (Slot *s : slots) dims.push_back({s->H, s->W});
     std::sort(dims.begin(), dims.end());
     std::ostringstream key;
-    key << c.p_storage << '/' << c.fast_math << '/' << c.temporal_block << '/' << (one ? 1 : 0);
+    key << c.p_storage << '/' << c.fast_math << '/' << c.temporal_block << '/' << (one ? 1 : 0)
+        << '/' << c.pdl << '/' << c.tile;
     for (auto &d : dims) key << ';' << d.first << 'x' << d.second;
     auto it = plan->tune.find(key.str());
     if (it != plan->tune.end()) {
-        *shape = it->second.first;
-        *depth = it->second.second;
+        *shape = it->second.shape;
+        *depth = it->second.depth;
+        *pdl = it->second.pdl;
         return TVSPEC_OK;
     }
     double total_px = 0.0;
     for (Slot *s : slots) total_px += (double)s->H * s->W;
     struct Cand {
         int shape, depth;
+        bool pdl;
         LaunchSet ls;
         double cost = 1e300;
     };
@@ -473,16 +507,22 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
     auto release_all = [&]() {
         for (Cand &x : cs) x.ls.release();
     };
+    const bool large = total_px > (double)(1 << 22);
+    const int kReps = large ? 2 : 8;
+    const int rounds = large ? 1 : 2;
     for (size_t i = 0; i < cands.size(); ++i) {
-        cs[i].shape = cands[i];
-        cs[i].depth = default_depth(c, cands[i]);
+        cs[i].shape = cands[i].first;
+        cs[i].pdl = cands[i].second;
+        cs[i].depth = default_depth(c, cs[i].shape);
         std::vector<ImgDesc> descs;
         for (Slot *s : slots) {
             ImgDesc d = slot_desc(*s, 0);
-            d.n_inner = cs[i].depth;  // every tile runs exactly `depth` iterations in launch 0
+            // kReps full launches of `depth` iterations, each reading what the previous one
+            // wrote (the chain a step runs)
+            d.n_inner = cs[i].depth * kReps;
             descs.push_back(d);
         }
-        tvspec_status s = launchset_build(&cs[i].ls, descs, cands[i], cs[i].depth);
+        tvspec_status s = launchset_build(&cs[i].ls, descs, cs[i].shape, cs[i].depth);
         if (s != TVSPEC_OK) {
             release_all();
             return s;
@@ -494,9 +534,6 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
     // the first round also brings the GPU to its working clock. A large set (several waves of
     // tiles per launch) times well with fewer launches: one round of graphs of 2 launches, so
     // that tuning stays a few launches per candidate.
-    const bool large = total_px > (double)(1 << 22);
-    const int kReps = large ? 2 : 8;
-    const int rounds = large ? 1 : 2;
     std::vector<cudaGraphExec_t> execs(cs.size(), nullptr);
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < cs.size() && e == cudaSuccess; ++i) {
@@ -506,10 +543,10 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
         if (e != cudaSuccess) break;
         cudaError_t le = cudaSuccess;
         for (int r = 0; r < kReps && le == cudaSuccess; ++r)
-            le = one ? launch_tiled_one(x.shape, c.p_storage, c.fast_math != 0, x.ls.h_descs[0], 0, 0,
-                                        x.depth, c.tau, st)
+            le = one ? launch_tiled_one(x.shape, c.p_storage, c.fast_math != 0, x.ls.h_descs[0], 0, r,
+                                        x.depth, c.tau, st, x.pdl)
                      : launch_tiled(x.shape, c.p_storage, c.fast_math != 0, x.ls.d_tiles, nt,
-                                    x.ls.d_descs, 0, 0, x.depth, c.tau, st);
+                                    x.ls.d_descs, 0, r, x.depth, c.tau, st, x.pdl);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
         if (e == cudaSuccess) e = le;
@@ -541,10 +578,12 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
     const Cand *best = &cs[0];
     for (const Cand &x : cs)
         if (x.cost < best->cost) best = &x;
-    plan->tune[key.str()] = {best->shape, best->depth};
-    tune_cache_append(plan, key.str(), best->shape, best->depth);
+    const bool use_pdl = pdl_rule(best->shape);
+    plan->tune[key.str()] = {best->shape, best->depth, use_pdl};
+    tune_cache_append(plan, key.str(), best->shape, best->depth, use_pdl);
     *shape = best->shape;
     *depth = best->depth;
+    *pdl = use_pdl;
     return TVSPEC_OK;
 }
 
@@ -596,10 +635,10 @@ static tvspec_status enqueue_iterations(tvspec_plan *plan, LaunchSet &ls,
     for (int b = 0; b < nblk; ++b) {
         cudaError_t e = one ? launch_tiled_one(ls.shape, c.p_storage, c.fast_math != 0,
                                                ls.h_descs[0], gstep, b, ls.depth, c.tau, st,
-                                               c.pdl != 0)
+                                               ls.pdl)
                             : launch_tiled(ls.shape, c.p_storage, c.fast_math != 0, ls.d_tiles,
                                            nt, ls.d_descs, gstep, b, ls.depth, c.tau, st,
-                                           c.pdl != 0);
+                                           ls.pdl);
         if (e != cudaSuccess) return fail_cuda(e, "tiled kernel launch");
         ++*nk;
     }
@@ -622,12 +661,12 @@ tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *>
     tvspec_status s = enqueue_iterations(plan, ls, slots, n_active, gstep, st, nk);
     if (s != TVSPEC_OK) return s;
     const int ep_depth = ls.shape < 0 ? 1 : ls.depth;
-    cudaError_t e = (ls.n == 1 && n_active == 1)
-                        ? launch_epilogue_one(c.p_storage, ls.h_descs[0], gstep, ep_depth, st,
-                                              c.pdl != 0)
+    const bool one_ep = ls.n == 1 && n_active == 1;
+    const bool pdl = ls.pdl;
+    cudaError_t e = one_ep
+                        ? launch_epilogue_one(c.p_storage, ls.h_descs[0], gstep, ep_depth, st, pdl)
                         : launch_epilogue(c.p_storage, ls.d_descs, ls.d_ep_img, ls.d_ep_base,
-                                          ls.ep_prefix[n_active], gstep, ep_depth, st,
-                                          c.pdl != 0);
+                                          ls.ep_prefix[n_active], gstep, ep_depth, st, pdl);
     if (e != cudaSuccess) return fail_cuda(e, "epilogue launch");
     if (ls.ep_prefix[n_active] > 0) ++*nk;
     return TVSPEC_OK;
@@ -656,9 +695,10 @@ static tvspec_status enqueue_step_split(tvspec_plan *plan, LaunchSet &ls, std::v
     const int ep_depth = ls.shape < 0 ? 1 : ls.depth;
     const bool one = ls.n == 1 && n_active == 1;
     const int nblk = ls.ep_prefix[n_active];
-    cudaError_t e = one ? launch_epi_primal_one(c.p_storage, ls.h_descs[0], gstep, ep_depth, st, c.pdl != 0)
+    const bool pdl = ls.pdl;
+    cudaError_t e = one ? launch_epi_primal_one(c.p_storage, ls.h_descs[0], gstep, ep_depth, st, pdl)
                         : launch_epi_primal(c.p_storage, ls.d_descs, ls.d_ep_img, ls.d_ep_base, nblk,
-                                            gstep, ep_depth, st, c.pdl != 0);
+                                            gstep, ep_depth, st, pdl);
     if (e != cudaSuccess) return fail_cuda(e, "epilogue launch");
     if (nblk > 0) ++*nk;
     if (gstep >= 1 && nblk > 0) {  // phi from the second step on (every image here has s0 = 0)
@@ -806,8 +846,9 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
     std::vector<Slot *> sp;
     for (int i = 0; i < E->n_tiled; ++i) sp.push_back(&E->slots[i]);
     int shape = -1, depth = 1;
+    bool pdl = false;
     tvspec_status st = TVSPEC_OK;
-    if (!sp.empty()) st = choose_tiles(plan, sp, plan->stream, &shape, &depth);
+    if (!sp.empty()) st = choose_tiles(plan, sp, plan->stream, &shape, &depth, false, &pdl);
     else if (plan->cfg.kernel != TVSPEC_KERNEL_NAIVE) shape = 0, depth = 1;
     if (st != TVSPEC_OK) {
         free_entry(*E, plan->stream);
@@ -835,6 +876,7 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
         free_entry(*E, plan->stream);
         return st;
     }
+    E->ls.pdl = pdl;
     if (cudaMallocHost((void **)&E->h_status, sizeof(unsigned) * n) != cudaSuccess) {
         free_entry(*E, plan->stream);
         return fail(TVSPEC_ENOMEM, "pinned status words");
@@ -1046,14 +1088,14 @@ static tvspec_status scratch_slot(tvspec_plan *plan, int H, int W, Slot **out) {
     return TVSPEC_OK;
 }
 
-tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *depth) {
+tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *depth, bool *pdl) {
     std::lock_guard<std::mutex> lock(plan->mu);
     TV_CK(cudaSetDevice(plan->device));
     Slot *sl = nullptr;
     tvspec_status s = scratch_slot(plan, H, W, &sl);
     if (s != TVSPEC_OK) return s;
     std::vector<Slot *> sp{sl};
-    s = choose_tiles(plan, sp, plan->stream, shape, depth, /*table_form=*/true);
+    s = choose_tiles(plan, sp, plan->stream, shape, depth, /*table_form=*/true, pdl);
     if (s != TVSPEC_OK) return s;
     TV_CK(cudaStreamSynchronize(plan->stream));
     return TVSPEC_OK;
@@ -1066,14 +1108,16 @@ tvspec_status run_iterations(tvspec_plan *plan, ImgDesc d, cudaStream_t st, int 
     tvspec_status s = scratch_slot(plan, d.H, d.W, &tune_slot);
     if (s != TVSPEC_OK) return s;
     int shape = -1, depth = 1;
+    bool pdl = false;
     std::vector<Slot *> sp{tune_slot};
-    s = choose_tiles(plan, sp, plan->stream, &shape, &depth);
+    s = choose_tiles(plan, sp, plan->stream, &shape, &depth, false, &pdl);
     if (s != TVSPEC_OK) return s;
     d.s0 = 0;
     d.K = std::max(d.K, 1);
     std::ostringstream key;
     key << d.p1[0] << '/' << d.p1[1] << '/' << d.p2[0] << '/' << d.p2[1] << '/' << d.gl << '/'
-        << d.H << 'x' << d.W << '/' << d.pitch << '/' << d.n_inner << '/' << shape << '/' << depth;
+        << d.H << 'x' << d.W << '/' << d.pitch << '/' << d.n_inner << '/' << shape << '/' << depth
+        << '/' << pdl;
     auto it = plan->iter_sets.find(key.str());
     LaunchSet *ls = nullptr;
     if (it == plan->iter_sets.end()) {
@@ -1088,6 +1132,7 @@ tvspec_status run_iterations(tvspec_plan *plan, ImgDesc d, cudaStream_t st, int 
             nls->release();
             return s;
         }
+        nls->pdl = pdl;
         ls = nls.get();
         plan->iter_sets[key.str()] = std::move(nls);
     } else {
@@ -1172,8 +1217,15 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
     p->cfg.tune_cache = nullptr;  // the plan keeps its own copy of the path
     p->tune_prefix = tune_prefix_for(device);
     tune_cache_load(p);
-    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    // the spectral part of the split epilogue runs on a low-priority stream beside the next
+    // step's dual iterations (the critical path), which keep the higher priority
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
+    e = cudaStreamCreateWithPriority(&p->stream, cudaStreamNonBlocking, prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, prio_low);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {

@@ -73,6 +73,7 @@ ImgDesc slot_desc(const Slot &s, int s0);
 // each image so that a prefix of the images maps to a prefix of each table.
 struct LaunchSet {
     int n = 0, shape = -1, depth = 0;
+    bool pdl = false;  // programmatic dependent launch for this set's kernels (autotuned)
     ImgDesc *d_descs = nullptr;
     TileRef *d_tiles = nullptr;
     int *d_ep_img = nullptr, *d_ep_base = nullptr;
@@ -105,6 +106,12 @@ struct CacheEntry {
 
 struct Server;  // serving scheduler (serving.cu)
 
+// The autotuner's choice for a set of image sizes.
+struct TuneChoice {
+    int shape = -1, depth = 1;
+    bool pdl = false;
+};
+
 }  // namespace tvspec
 
 struct tvspec_plan {
@@ -120,7 +127,7 @@ struct tvspec_plan {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::mutex mu;  // serialises the plain and batched paths
     std::list<std::unique_ptr<tvspec::CacheEntry>> cache;  // most recent first
-    std::map<std::string, std::pair<int, int>> tune;         // key -> (shape, depth)
+    std::map<std::string, tvspec::TuneChoice> tune;          // key -> (shape, depth, pdl)
     std::string tune_cache;   // file keeping tune across processes ("" = none)
     double *h_word = nullptr; // page-locked scalar for small device-to-host reads (plan->mu held)
     std::string tune_prefix;  // this GPU model and shape table, first field of the file lines
@@ -137,8 +144,9 @@ namespace tvspec {
 
 // Chooses (shape, depth) for a set of slots (autotuned unless the config fixes them).
 // table_form: time the tile-table kernel even for one image (the serving path always uses it).
+// *pdl (if given) receives whether programmatic dependent launch paid for the chosen shape.
 tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, cudaStream_t st,
-                           int *shape, int *depth, bool table_form = false);
+                           int *shape, int *depth, bool table_form = false, bool *pdl = nullptr);
 
 // Enqueues the device work of one ROF step at global step gstep for the first n_active images
 // of the set (dual iterations + epilogue). Adds the kernels launched to *n_kernels.
@@ -161,6 +169,7 @@ tvspec_status order_after(cudaStream_t later, cudaStream_t earlier);
 tvspec_status run_iterations(tvspec_plan *plan, ImgDesc d, cudaStream_t st, int *final_copy);
 
 // Tile choice for an H x W image, tuned on plan-owned scratch buffers (takes the plan lock).
-tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *depth);
+tvspec_status tune_for_size(tvspec_plan *plan, int H, int W, int *shape, int *depth,
+                            bool *pdl = nullptr);
 
 }  // namespace tvspec

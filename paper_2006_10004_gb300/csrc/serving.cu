@@ -63,6 +63,7 @@ struct Server {
     int cur = 0;
     int gstep = 0;
     int shape = -2, depth = 1;
+    bool pdl = false;
     void loop();
     void retire_loop();
     void hand_to_retire(const std::shared_ptr<ServeReq> &r, tvspec_status pending);
@@ -245,8 +246,8 @@ void Server::loop() {
             // that carries most of the served pixels (every shape gives the same bits)
             if (c.tile >= 0) {
                 std::vector<Slot *> none;
-                if (choose_tiles(plan, none, st, &shape, &depth, true) != TVSPEC_OK) shape = -2;
-            } else if (tune_for_size(plan, 2048, 2048, &shape, &depth) != TVSPEC_OK) {
+                if (choose_tiles(plan, none, st, &shape, &depth, true, &pdl) != TVSPEC_OK) shape = -2;
+            } else if (tune_for_size(plan, 2048, 2048, &shape, &depth, &pdl) != TVSPEC_OK) {
                 shape = -2;
             }
             if (shape == -2) {
@@ -259,6 +260,7 @@ void Server::loop() {
             if (ls_used[nb]) cudaEventSynchronize(ls_ev[nb]);  // its last tick is done
             std::vector<ImgDesc> descs;
             for (auto &r : active) descs.push_back(slot_desc(r->slot, r->s0));
+            ls[nb].pdl = pdl;
             if (launchset_build(&ls[nb], descs, shape, depth) != TVSPEC_OK) {
                 fail_all_active(TVSPEC_ECUDA);
                 continue;

@@ -125,6 +125,8 @@ cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *til
 // The same pass over the tiles of one image whose descriptor is passed by value (no table
 // reads before the tile loads). Available for p_storage 0 (tiled_one_available).
 bool tiled_one_available(int p_storage);
+// CTAs of the tiled kernel of a shape that fit on one SM (occupancy, asked once per kernel).
+int tiled_ctas_per_sm(int shape, int p_storage, bool fast, bool one);
 cudaError_t launch_tiled_one(int shape, int p_storage, bool fast, const ImgDesc &d, int gstep,
                              int blk, int depth, float tau, cudaStream_t st, bool pdl = false);
 

@@ -429,10 +429,10 @@ def test_tune_cache_file_round_trip(tv, tmp_path):
     with tv.Plan(0, tune_cache=path) as a:
         ra = a.decompose(*args)
     lines = open(path).read().split("\n")
-    prefix, key, shape, depth = lines[0].split()
+    prefix, key, shape, depth, pdl = lines[0].split()  # pdl: dependent launch chosen or not
     forced = 3 if int(shape) != 3 else 2
     with open(path, "w") as fh:
-        fh.write(f"{prefix} {key} {forced} 4\n")
+        fh.write(f"{prefix} {key} {forced} 4 0\n")
         fh.write(f"another-gpu/sm1/shapes1-0 {key} 0 1\n")  # ignored: other GPU / build
     with tv.Plan(0, tune_cache=path) as b:
         rb = b.decompose(*args)
