@@ -314,7 +314,9 @@ def run_gb300(args):
         s1 = plan.stats()
         n_launch = int(s1["kernel_launches"] - s0["kernel_launches"])
         per_launch_s = e0.elapsed_time(e1) / 1000.0 / max(n_launch, 1)
-        alg_bytes = ALG_BYTES_FP32 * H * W * depth
+        # n_inner need not be a multiple of the temporal block (300 = 37 x 8 + 4): the bytes of
+        # an average launch are those of all iterations over all launches
+        alg_bytes = ALG_BYTES_FP32 * H * W * iters * reps / max(n_launch, 1)
         achieved = alg_bytes / per_launch_s / 1e9
         peak, src = _peaks()
         traffic = None
@@ -329,7 +331,8 @@ def run_gb300(args):
                               "frac": achieved / peak, "traffic": traffic,
                               "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
                               "kernel": "k_tiled", "per_launch_us": per_launch_s * 1e6,
-                              "iters_per_launch": depth,
+                              "temporal_block": depth,
+                              "iters_per_launch": iters * reps / max(n_launch, 1),
                               "algorithmic_bytes_per_launch": alg_bytes}
 
     # ---- CPU baseline: the FP64 oracle on this host -------------------------------------------

@@ -247,7 +247,8 @@ tvspec_status tvspec_submit(tvspec_plan *plan, const tvspec_request *req, uint64
 
 /* OK when the request finished (outputs written), ENOTREADY while queued or running,
  * ECANCELLED, or the request's own error status. EINVAL for an unknown ticket. A finished
- * ticket stays queryable until the plan is destroyed. Thread-safe. */
+ * ticket stays queryable until the plan is destroyed; it then holds its status only (its
+ * workspace and band / filter tables are released when it finishes). Thread-safe. */
 tvspec_status tvspec_poll(tvspec_plan *plan, uint64_t ticket);
 
 /* Wait up to timeout_ms (< 0: no limit) for the request; returns like tvspec_poll, or

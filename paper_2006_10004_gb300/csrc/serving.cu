@@ -71,6 +71,11 @@ struct Server {
 };
 
 static void finish(Server *S, const std::shared_ptr<ServeReq> &r, tvspec_status result) {
+    // a finished ticket stays queryable; it keeps its status, not its request's tables
+    std::vector<double>().swap(r->job.edges);
+    std::vector<signed char>().swap(r->job.band_of_k);
+    std::vector<double>().swap(r->job.filt_H);
+    std::vector<double>().swap(r->job.filt_res);
     std::lock_guard<std::mutex> lk(S->mu);
     r->result = result;
     r->state = 2;
