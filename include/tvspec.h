@@ -76,7 +76,10 @@ typedef struct {
     int use_graphs;         /* 1 (default): a problem signature used a second time is captured into
                                a CUDA graph then and replayed from then on (plan-level LRU of 4) */
     int fast_math;          /* 1 (default): hardware approximate sqrt/reciprocal; 0: IEEE-rounded */
-    size_t mem_budget_bytes;/* device memory the serving scheduler may hold; 0 = 60 GiB */
+    size_t mem_budget_bytes;/* device memory the serving scheduler may hold, and the bound on
+                             * the batch workspaces a plan keeps cached for reuse (least
+                             * recently used ones are freed first; a batch needing more than
+                             * the budget still runs, alone); 0 = 60 GiB */
     int max_batch;          /* serving: most requests resident at once; 0 = 256 */
     int pdl;                /* 1 (default): programmatic dependent launch between the kernels of a
                                step (the next kernel is scheduled while the previous one drains;

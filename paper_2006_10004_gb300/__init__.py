@@ -495,7 +495,10 @@ class Plan:
         return t.value, out
 
     def poll(self, ticket: int) -> int:
-        return int(self._lib.tvspec_poll(self._h, ctypes.c_uint64(ticket)))
+        s = int(self._lib.tvspec_poll(self._h, ctypes.c_uint64(ticket)))
+        if s != ENOTREADY:
+            self._keep.pop(ticket, None)  # finished: the library no longer writes its buffers
+        return s
 
     def wait(self, ticket: int, timeout_ms: int = -1) -> int:
         s = int(self._lib.tvspec_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms)))

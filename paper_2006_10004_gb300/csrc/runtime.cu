@@ -797,7 +797,20 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
     }
     // new entry: workspace, tile choice, tables, optionally a captured graph
     TV_CK(cudaStreamSynchronize(plan->stream));
-    while (plan->cache.size() >= 4) {
+    // least recently used entries leave while there are four, or while the cached workspaces
+    // and the new one together exceed the memory budget (an entry larger than the budget on its
+    // own still runs, alone)
+    const bool naive_cfg = plan->cfg.kernel == TVSPEC_KERNEL_NAIVE;
+    size_t need = 0;
+    for (const Job &j : jobs) need += slot_bytes_for(j, plan->cfg.p_storage, naive_cfg);
+    auto cached_bytes = [&]() {
+        size_t b = 0;
+        for (auto &e : plan->cache)
+            for (const Slot &x : e->slots) b += x.bytes;
+        return b;
+    };
+    while (!plan->cache.empty() &&
+           (plan->cache.size() >= 4 || cached_bytes() + need > plan_budget(plan))) {
         free_entry(*plan->cache.back(), plan->stream);
         plan->cache.pop_back();
     }
@@ -835,6 +848,19 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
         Slot s;
         tvspec_status st = slot_alloc(&s, jobs[E->order[i]], plan->cfg.p_storage, naive,
                                       plan->stream, false, plan->cfg.acc_mode);
+        if (st == TVSPEC_ENOMEM && !plan->cache.empty()) {
+            // out of device memory with other workspaces cached: drop them all, start over
+            free_entry(*E, plan->stream);
+            E->slots.clear();
+            E->maxK = 0;
+            while (!plan->cache.empty()) {
+                free_entry(*plan->cache.back(), plan->stream);
+                plan->cache.pop_back();
+            }
+            cudaGetLastError();
+            i = -1;
+            continue;
+        }
         if (st != TVSPEC_OK) {
             free_entry(*E, plan->stream);
             return st;

@@ -408,6 +408,30 @@ def test_serving_budget_and_cancel(tv):
         assert p.poll(12345) == tv.EINVAL
 
 
+def test_cached_batch_workspaces_stay_within_the_budget(tv):
+    imgs = [_img(120 + 10 * i, 130, 60 + i) for i in range(6)]
+    a = [(imgs[i], 0.5, 5, 20, syn.DYADIC_EDGES) for i in range(3)]
+    b = [(imgs[i], 0.5, 6, 20, syn.DYADIC_EDGES) for i in range(3, 6)]
+    with tv.Plan(0) as p0:
+        want_a = p0.decompose_batch(a)
+        bytes_a = p0.stats()["workspace_bytes"]
+        want_b = p0.decompose_batch(b)
+        assert p0.stats()["workspace_bytes"] > bytes_a  # both kept under the default budget
+    budget = int(1.6 * bytes_a)
+    with tv.Plan(0, mem_budget_bytes=budget) as p:
+        for x, y in zip(p.decompose_batch(a), want_a):
+            _same(x, y)
+        for x, y in zip(p.decompose_batch(b), want_b):
+            _same(x, y)
+        assert p.stats()["workspace_bytes"] <= budget  # a's workspace made room for b's
+        both = p.decompose_batch(a + b)  # larger than the budget on its own: runs alone
+        assert p.stats()["workspace_bytes"] > budget
+        for x, y in zip(both, want_a + want_b):
+            _same(x, y)
+        for x, y in zip(p.decompose_batch(a), want_a):
+            _same(x, y)
+
+
 def test_invalid_arguments_leave_plan_usable(plan, tv):
     f = _img(16, 16, 40)
     with pytest.raises(tv.TvSpecError) as ei:
