@@ -4,6 +4,8 @@ Parity bars are in ``tolerances.py``. Bit-identity tests check what the design p
 the result of the float32 dual iterations does not depend on the tile shape, the iterations
 per launch, graph replay, the memory mode, or the batch an image runs in.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -311,6 +313,58 @@ def test_config1_full_size_parity(plan):
     ref = oracle.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True)
     m = assert_parity(g, ref, job.f, "config1")
     print("config1", m)
+
+
+def test_m1024_full_size_parity_as_benchmarked(plan):
+    # the 1024^2 workload of the decompositions/s figure, whole (K=50, 300 iterations), from
+    # device memory on a side stream as the bench runs it
+    import torch
+
+    job = syn.m1024().jobs[0]
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        g = plan.decompose(torch.from_numpy(job.f).cuda(), job.dt, job.K, job.n_inner, job.edges,
+                           stream=st)
+    st.synchronize()
+    g = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in g.items()}
+    ref = oracle.decompose(job.f, job.dt, job.K, job.n_inner, job.edges)
+    print("m1024", assert_parity(g, ref, job.f, "m1024"))
+
+
+def test_maximum_size_sampled_parity(plan):
+    # the largest image the ABI accepts (H*W = 2^28), checked where the oracle can follow it. An
+    # iteration moves information at most one pixel (w reads p one pixel up / left, the update
+    # reads w one pixel down / right, u_{k+1} reads p one pixel up / left), so after K steps of
+    # n_inner iterations an output depends only on inputs within K (n_inner + 1) pixels: the
+    # oracle run on a window with a wider margin reproduces the window's centre. Plus exact
+    # reconstruction everywhere and S against the band it feeds.
+    H = W = 1 << 14
+    K, n_inner, dt = 2, 2, 0.5
+    edges = [0.0, 1.0, math.inf]
+    rng = np.random.default_rng(2024)
+    f = rng.standard_normal((H, W), dtype=np.float32)
+    f[1000:3000, 5000:9000] += 4.0
+    f[H - 700:, :300] -= 3.0
+    g = plan.decompose(f, dt, K, n_inner, edges)
+    scale = float(np.abs(f).max())
+    for y0 in range(0, H, 2048):  # reconstruction, in slabs
+        sl = slice(y0, y0 + 2048)
+        rec = g["bands"][:, sl].astype(np.float64).sum(0) + g["residual"][sl]
+        assert np.abs(rec - f[sl]).max() <= 1e-5 * scale
+    # K = 2: S(t_1) = sum |phi_1|, and band 0 holds phi_1 dt (t_1 = 0.5 in [0, 1))
+    s_band = np.abs(g["bands"][0].astype(np.float64)).sum() / dt
+    assert abs(g["S"][0] - s_band) <= 1e-5 * g["S"][0]
+    m = K * (n_inner + 1) + 4
+    side = 48
+    for y0, x0 in ((0, 0), (H - side, W - side), (0, W // 2), (1000 - side // 2, 5000 - side // 2),
+                   (H // 2 + 7, 123)):
+        ya, yb = max(0, y0 - m), min(H, y0 + side + m)
+        xa, xb = max(0, x0 - m), min(W, x0 + side + m)
+        ref = oracle.decompose(f[ya:yb, xa:xb], dt, K, n_inner, edges)
+        cy, cx = slice(y0 - ya, y0 - ya + side), slice(x0 - xa, x0 - xa + side)
+        gy, gx = slice(y0, y0 + side), slice(x0, x0 + side)
+        assert np.abs(g["bands"][:, gy, gx] - ref["bands"][:, cy, cx]).max() <= 1e-3 * scale
+        assert np.abs(g["residual"][gy, gx] - ref["residual"][cy, cx]).max() <= 1e-3 * scale
 
 
 def test_config3_full_size_first_steps_parity(plan):
