@@ -110,6 +110,10 @@ typedef struct {
                                another GPU model or library build are ignored), one line appended
                                per new choice; NULL (default) = in-memory only. The string is
                                copied by tvspec_plan_create. */
+    int test_fail_alloc;    /* fault injection for tests, on the host: n > 0 makes the plan's
+                               n-th batch-workspace allocation (counted from 1 over the plan's
+                               life) fail once with TVSPEC_ENOMEM, as if the device were out of
+                               memory; default 0 (off) */
 } tvspec_config;
 
 /* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in

@@ -495,6 +495,7 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
         *pdl = it->second.pdl;
         return TVSPEC_OK;
     }
+    NvtxRange range("tvspec autotune");
     double total_px = 0.0;
     for (Slot *s : slots) total_px += (double)s->H * s->W;
     struct Cand {
@@ -846,8 +847,12 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
     if (naive && n != 1) return fail(TVSPEC_ENOTSUP, "the reference kernel runs one image at a time");
     for (int i = 0; i < n; ++i) {
         Slot s;
-        tvspec_status st = slot_alloc(&s, jobs[E->order[i]], plan->cfg.p_storage, naive,
-                                      plan->stream, false, plan->cfg.acc_mode);
+        tvspec_status st;
+        if (plan->cfg.test_fail_alloc > 0 && ++plan->alloc_count == (uint64_t)plan->cfg.test_fail_alloc)
+            st = fail(TVSPEC_ENOMEM, "injected workspace allocation failure (test_fail_alloc)");
+        else
+            st = slot_alloc(&s, jobs[E->order[i]], plan->cfg.p_storage, naive, plan->stream, false,
+                            plan->cfg.acc_mode);
         if (st == TVSPEC_ENOMEM && !plan->cache.empty()) {
             // out of device memory with other workspaces cached: drop them all, start over
             free_entry(*E, plan->stream);
@@ -1000,6 +1005,7 @@ tvspec_status order_after(cudaStream_t later, cudaStream_t earlier) {
 }
 
 static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStream_t user_st) {
+    NvtxRange range(jobs.size() == 1 ? "tvspec decompose" : "tvspec decompose_batch");
     std::lock_guard<std::mutex> lock(plan->mu);
     TV_CK(cudaSetDevice(plan->device));
     const int mk = jobs[0].r.mem_kind;
@@ -1206,6 +1212,7 @@ void tvspec_config_init(tvspec_config *cfg) {
     cfg->persistent = 0;
     cfg->barrier_timeout_ms = 2000;
     cfg->test_barrier_noshow = -1;
+    cfg->test_fail_alloc = 0;
     cfg->resident = 1;
     cfg->resident_variant = -1;
 }

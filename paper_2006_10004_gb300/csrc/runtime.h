@@ -14,10 +14,21 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tvspec.h"
 #include "tvspec_internal.h"
 
 namespace tvspec {
+
+// A named NVTX range over a scope: the host runtime's phases (calls, autotuning, graph
+// replays, serving ticks) show up by name in profilers; without one attached it costs nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Records msg as the thread's last error and returns s.
 tvspec_status fail(tvspec_status s, const std::string &msg);
@@ -136,6 +147,7 @@ struct tvspec_plan {
     std::atomic<uint64_t> kernel_launches{0}, graph_launches{0}, graphs_built{0},
         decompositions{0};
     std::atomic<int> last_tile{-1}, last_depth{0};
+    uint64_t alloc_count = 0;  // batch-workspace allocations so far (test_fail_alloc; plan->mu held)
     tvspec::Server *server = nullptr;  // created on first submit, freed by tvspec_server_stop
     std::mutex server_mu;
 };

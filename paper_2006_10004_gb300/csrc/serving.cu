@@ -285,6 +285,7 @@ void Server::loop() {
             }
             changed = false;
         }
+        NvtxRange tick("tvspec serving step");
         std::vector<Slot *> sp;
         for (auto &r : active) sp.push_back(&r->slot);
         uint64_t nk = 0;

@@ -496,6 +496,7 @@ static tvspec_status rof_solve_locked(tvspec_plan *plan, tvspec_rof_request &q, 
 using namespace tvspec;
 
 extern "C" tvspec_status tvspec_rof_solve(tvspec_plan *plan, tvspec_rof_request *req, void *stream) {
+    NvtxRange range("tvspec rof_solve");
     if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
     if (!req) return fail(TVSPEC_EINVAL, "request is NULL");
     tvspec_status s = check_rof_request(*req);

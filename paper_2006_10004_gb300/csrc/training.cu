@@ -367,6 +367,7 @@ using namespace tvspec;
 
 extern "C" tvspec_status tvspec_training_set(tvspec_plan *plan, const tvspec_training_request *req,
                                              void *stream) {
+    NvtxRange range("tvspec training_set");
     if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
     if (!req) return fail(TVSPEC_EINVAL, "request is NULL");
     tvspec_status s = check_training(*req);

@@ -40,6 +40,26 @@ def test_status_strings_and_version():
     assert b"sm_103a" in lib.tvspec_version()
 
 
+def test_config_layout_and_defaults_match_the_header():
+    # tvspec_config_init writes every field of the C struct: run it on a Config followed by a
+    # guard region; the binding's struct must end where the C one does (guard untouched, last
+    # field written) and hold the documented defaults
+    import ctypes
+
+    n = ctypes.sizeof(tv.Config)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    tv.load().tvspec_config_init(ctypes.cast(buf, ctypes.POINTER(tv.Config)))
+    assert bytes(buf[n:]) == b"\xab" * 64
+    c = tv.Config.from_buffer(buf)
+    want = dict(p_storage=0, warm_start=1, kernel=0, tile=-1, temporal_block=0, use_graphs=1,
+                fast_math=1, mem_budget_bytes=0, max_batch=0, pdl=1, persistent=0,
+                barrier_timeout_ms=2000, test_barrier_noshow=-1, resident=1, resident_variant=-1,
+                acc_mode=0, tune_cache=None, test_fail_alloc=0)
+    for k, v in want.items():
+        assert getattr(c, k) == v, k
+    assert abs(c.tau - 0.125) < 1e-9
+
+
 def test_tile_table():
     shapes = tv.tile_shapes()
     assert len(shapes) >= 8

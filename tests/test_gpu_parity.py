@@ -486,6 +486,32 @@ def test_cached_batch_workspaces_stay_within_the_budget(tv):
             _same(x, y)
 
 
+def test_injected_workspace_allocation_failure(tv):
+    # host-side fault injection (no device fault): the plan's n-th workspace allocation fails
+    # once with ENOMEM. With other workspaces cached the plan drops them and retries; with none
+    # the call reports ENOMEM and the plan stays usable.
+    a = [(_img(90 + 5 * i, 100, 70 + i), 0.5, 4, 20, syn.DYADIC_EDGES) for i in range(3)]
+    b = [(_img(60, 80 + 3 * i, 80 + i), 0.5, 5, 20, syn.DYADIC_EDGES) for i in range(2)]
+    with tv.Plan(0) as p0:
+        want_a = p0.decompose_batch(a)
+        want_b = p0.decompose_batch(b)
+    with tv.Plan(0, test_fail_alloc=4) as p:  # a takes allocations 1-3, b's first one fails
+        for x, y in zip(p.decompose_batch(a), want_a):
+            _same(x, y)
+        for x, y in zip(p.decompose_batch(b), want_b):
+            _same(x, y)
+        assert p.stats()["workspace_bytes"] > 0
+        for x, y in zip(p.decompose_batch(a), want_a):  # rebuilt after the eviction
+            _same(x, y)
+    with tv.Plan(0, test_fail_alloc=2) as p:  # nothing cached to give back: the call fails
+        with pytest.raises(tv.TvSpecError) as ei:
+            p.decompose_batch(a)
+        assert ei.value.status == tv.ENOMEM
+        assert p.stats()["workspace_bytes"] == 0
+        for x, y in zip(p.decompose_batch(a), want_a):
+            _same(x, y)
+
+
 def test_invalid_arguments_leave_plan_usable(plan, tv):
     f = _img(16, 16, 40)
     with pytest.raises(tv.TvSpecError) as ei:
