@@ -271,6 +271,30 @@ tvspec_status tvspec_cancel(tvspec_plan *plan, uint64_t ticket);
 tvspec_status tvspec_serving_stats(tvspec_plan *plan, int reset, uint64_t *count, double *p50_ms,
                                    double *p99_ms);
 
+/* Checkpoint / resume of one decomposition. The implicit-Euler flow (Eq. TVflow, one Eq. ROF
+ * solve per step) is deterministic, so a request can stop after any ROF step, its state can
+ * wait in host memory (or another process), and the run can continue from it to the same bits
+ * as an uninterrupted tvspec_decompose_ex of the same request on a plan of the same
+ * configuration.
+ *
+ * tvspec_checkpoint_bytes: size in bytes of the state of req under this plan's configuration
+ * (a header, then the image's whole device workspace: about 62 + 4 n_bands bytes per pixel);
+ * 0 for a NULL or invalid argument.
+ *
+ * tvspec_decompose_steps: runs ROF steps [k_begin, k_end) of req, 0 <= k_begin < k_end <= K.
+ * k_begin == 0 starts from req->f; otherwise state_in (host memory, written by a call that
+ * stopped at k_begin) is restored and req->f is not read. k_end < K: the state after step
+ * k_end - 1 goes to state_out (host memory, tvspec_checkpoint_bytes(plan, req) bytes, owned
+ * by the caller) and the request's outputs are not written; k_end == K: the outputs are
+ * written as by tvspec_decompose_ex (req->mem_kind) and state_out is not used. Synchronous,
+ * on the plan's stream. EINVAL for a bad range, a missing state buffer, or a state_in of
+ * another request, configuration or step; ENOTSUP when the plan runs the request on the
+ * one-CTA resident kernel (resident = 2), which has no step boundary; ECUDA for a non-finite
+ * value in the flow. */
+size_t tvspec_checkpoint_bytes(tvspec_plan *plan, const tvspec_request *req);
+tvspec_status tvspec_decompose_steps(tvspec_plan *plan, const tvspec_request *req, int k_begin,
+                                     int k_end, const void *state_in, void *state_out);
+
 /* One ROF step (Eq. ROF) by n_iter Chambolle iterations on the plan's kernel: u = g - lambda div p.
  * g (H*W), p1/p2 (H*W, in: starting dual field, out: final) and u (H*W, out) are contiguous
  * float32 buffers in host or device memory per mem_kind. Synchronous for host memory.

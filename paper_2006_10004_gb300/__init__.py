@@ -118,6 +118,9 @@ _SIGS = {
     "tvspec_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "tvspec_serving_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                             _dp, _dp]),
+    "tvspec_checkpoint_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.POINTER(Request)]),
+    "tvspec_decompose_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "tvspec_rof_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -424,6 +427,43 @@ class Plan:
         st = _stream_ptr(stream) if MEM_DEVICE in kinds else None
         _check(self._lib.tvspec_decompose_batch(self._h, len(reqs), arr, st), "tvspec_decompose_batch")
         return outs
+
+    # ---- checkpoint / resume -------------------------------------------------------------------
+    def checkpoint_bytes(self, f, dt: float, K: int, n_inner: int, edges, trace: bool = False,
+                         filters=None, parseval: bool = False) -> int:
+        """Bytes of a decomposition's saved state under this plan's configuration."""
+        keep = []
+        r, _, _ = self._make_request(f, dt, K, n_inner, edges, trace, keep, filters, parseval)
+        n = int(self._lib.tvspec_checkpoint_bytes(self._h, ctypes.byref(r)))
+        if n == 0:
+            raise TvSpecError(EINVAL, "tvspec_checkpoint_bytes", "invalid request")
+        return n
+
+    def decompose_steps(self, f, dt: float, K: int, n_inner: int, edges, k_begin: int, k_end: int,
+                        state=None, trace: bool = False, filters=None, parseval: bool = False):
+        """ROF steps [k_begin, k_end) of one decomposition. From k_begin > 0 it resumes from
+        ``state`` (a uint8 array returned by an earlier call that stopped at k_begin). Returns
+        (Result, None) when k_end == K, else (None, state after step k_end - 1)."""
+        keep = []
+        r, out, kind = self._make_request(f, dt, K, n_inner, edges, trace, keep, filters, parseval)
+        state_out = None
+        if k_end < K:
+            n = int(self._lib.tvspec_checkpoint_bytes(self._h, ctypes.byref(r)))
+            if n == 0:
+                raise TvSpecError(EINVAL, "tvspec_checkpoint_bytes", "invalid request")
+            state_out = np.empty(n, np.uint8)
+        sin = None
+        if state is not None:
+            state = np.ascontiguousarray(state, dtype=np.uint8)
+            sin = state.ctypes.data
+        if kind == MEM_DEVICE:
+            import torch
+
+            torch.cuda.synchronize()  # the call runs on the plan's own stream
+        _check(self._lib.tvspec_decompose_steps(self._h, ctypes.byref(r), int(k_begin), int(k_end), sin,
+                                                None if state_out is None else state_out.ctypes.data),
+               "tvspec_decompose_steps")
+        return (out, None) if k_end == K else (None, state_out)
 
     # ---- training-data generation (Sec. 4.1) ---------------------------------------------------
     def training_set(self, sources, crops, size: int, standardize: int, dt: float, K: int, n_inner: int,

@@ -1348,6 +1348,142 @@ tvspec_status tvspec_decompose_batch(tvspec_plan *plan, int n, const tvspec_requ
     return run_jobs(plan, jobs, (cudaStream_t)stream);
 }
 
+// ---- checkpoint / resume ----------------------------------------------------------------
+// The state between two ROF steps is the image's whole workspace (u_{k-1}, u_k, both copies of
+// p, g/dt, the band and filter accumulators, the outputs written so far, S so far), saved
+// byte for byte after a header that ties it to the request, the configuration and the step.
+
+namespace {
+
+struct CheckpointHeader {
+    char magic[8];        // "TVSPCKP1"
+    uint64_t key_hash;    // FNV-1a of the job key (configuration + request signature)
+    uint64_t slot_bytes;  // workspace bytes that follow
+    int32_t k_next;       // the ROF step the state resumes at
+    int32_t launches;     // dual-iteration launches per step of the run that saved it
+    int32_t reserved[4];
+};
+
+const char kCheckpointMagic[8] = {'T', 'V', 'S', 'P', 'C', 'K', 'P', '1'};
+
+uint64_t fnv1a(const std::string &x) {
+    uint64_t h = 1469598103934665603ull;
+    for (unsigned char c : x) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+size_t tvspec_checkpoint_bytes(tvspec_plan *plan, const tvspec_request *req) {
+    if (!plan || !req) return 0;
+    Job j;
+    if (make_job(*req, &j) != TVSPEC_OK) return 0;
+    return sizeof(CheckpointHeader) +
+           slot_bytes_for(j, plan->cfg.p_storage, plan->cfg.kernel == TVSPEC_KERNEL_NAIVE);
+}
+
+tvspec_status tvspec_decompose_steps(tvspec_plan *plan, const tvspec_request *req, int k_begin,
+                                     int k_end, const void *state_in, void *state_out) {
+    NvtxRange range("tvspec decompose_steps");
+    if (!plan) return fail(TVSPEC_EINVAL, "plan is NULL");
+    if (!req) return fail(TVSPEC_EINVAL, "request is NULL");
+    std::vector<Job> jobs(1);
+    tvspec_status s = make_job(*req, &jobs[0]);
+    if (s != TVSPEC_OK) return s;
+    const tvspec_request &r = jobs[0].r;
+    if (k_begin < 0 || k_end <= k_begin || k_end > r.K)
+        return fail(TVSPEC_EINVAL, "need 0 <= k_begin < k_end <= K");
+    if (k_begin > 0 && !state_in) return fail(TVSPEC_EINVAL, "resuming needs state_in");
+    if (k_end < r.K && !state_out) return fail(TVSPEC_EINVAL, "stopping before K needs state_out");
+    std::lock_guard<std::mutex> lock(plan->mu);
+    TV_CK(cudaSetDevice(plan->device));
+    CacheEntry *E = nullptr;
+    s = get_entry(plan, jobs, &E);
+    if (s != TVSPEC_OK) return s;
+    if (E->n_tiled != 1)
+        return fail(TVSPEC_ENOTSUP, "the resident kernel runs whole decompositions (resident = 2)");
+    Slot &sl = E->slots[0];
+    // the key covers what decides the state's layout and bits, not the launch choices (tile
+    // shape, depth, graphs), which leave both unchanged
+    tvspec_config kc = plan->cfg;
+    kc.kernel = kc.kernel == TVSPEC_KERNEL_NAIVE ? TVSPEC_KERNEL_NAIVE : TVSPEC_KERNEL_AUTO;
+    kc.tile = -1;
+    kc.temporal_block = 0;
+    kc.use_graphs = 1;
+    const uint64_t key = fnv1a(job_key(kc, jobs));
+    const int launches = launches_per_step(r.n_inner, E->ls.shape < 0 ? 1 : E->ls.depth);
+    cudaStream_t st = plan->stream;
+    std::vector<Slot *> sp{&sl};
+    const cudaMemcpyKind in_kind = r.mem_kind == TVSPEC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind out_kind = r.mem_kind == TVSPEC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (k_begin == 0) {
+        TV_CK(cudaMemsetAsync(sl.base + sl.zero_off, 0, sl.zero_bytes, st));
+        TV_CK(cudaMemcpyAsync(sl.f, r.f, (size_t)r.H * r.W * 4, in_kind, st));
+        cudaError_t e = launch_init(E->ls.d_descs, E->ls.d_ep_img, E->ls.d_ep_base, E->ls.ep_prefix[1], st);
+        if (e != cudaSuccess) return fail_cuda(e, "init launch");
+        ++plan->kernel_launches;
+    } else {
+        CheckpointHeader h;
+        std::memcpy(&h, state_in, sizeof h);
+        if (std::memcmp(h.magic, kCheckpointMagic, 8) != 0 || h.key_hash != key ||
+            h.slot_bytes != sl.bytes || h.launches < 1)
+            return fail(TVSPEC_EINVAL, "state_in belongs to another request or configuration");
+        if (h.k_next != k_begin) return fail(TVSPEC_EINVAL, "state_in was saved at another step");
+        TV_CK(cudaMemcpyAsync(sl.base, static_cast<const char *>(state_in) + sizeof h, sl.bytes,
+                              cudaMemcpyHostToDevice, st));
+        // the copy of p that step k_begin reads depends on the launches per step (p_copy): if
+        // this plan's tile choice differs in their parity, move p to the copy it will read
+        const int was = p_copy(k_begin, h.launches, 0), now = p_copy(k_begin, launches, 0);
+        if (was != now) {
+            TV_CK(cudaMemcpyAsync(sl.p1[now], sl.p1[was], sl.p_bytes, cudaMemcpyDeviceToDevice, st));
+            TV_CK(cudaMemcpyAsync(sl.p2[now], sl.p2[was], sl.p_bytes, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    bool pending = false;
+    for (int g = k_begin; g < k_end; ++g) {
+        uint64_t nk = 0;
+        s = enqueue_step_split(plan, E->ls, sp, 1, g, st, &pending, &nk);
+        plan->kernel_launches += nk;
+        if (s != TVSPEC_OK) {
+            if (pending) cudaStreamWaitEvent(st, plan->ev_join, 0);
+            return s;
+        }
+    }
+    if (pending) TV_CK(cudaStreamWaitEvent(st, plan->ev_join, 0));
+    if (k_end < r.K) {
+        CheckpointHeader h{};
+        std::memcpy(h.magic, kCheckpointMagic, 8);
+        h.key_hash = key;
+        h.slot_bytes = sl.bytes;
+        h.k_next = k_end;
+        h.launches = launches;
+        std::memcpy(state_out, &h, sizeof h);
+        TV_CK(cudaMemcpyAsync(static_cast<char *>(state_out) + sizeof h, sl.base, sl.bytes,
+                              cudaMemcpyDeviceToHost, st));
+    } else {
+        const size_t N = (size_t)r.H * r.W;
+        const CopyItem out[] = {{sl.bands, r.bands, (size_t)sl.n_bands * N * 4},
+                                {sl.residual, r.residual, N * 4},
+                                {sl.S, r.S, (size_t)(r.K - 1) * 8},
+                                {sl.utrace, r.u_trace, r.u_trace ? (size_t)(r.K + 1) * N * 8 : 0},
+                                {sl.filtered, r.filtered, (size_t)r.n_filters * N * 4},
+                                {sl.S_par, r.S_parseval, r.S_parseval ? (size_t)(r.K - 1) * 8 : 0}};
+        for (const CopyItem &c : out)
+            if (c.bytes) TV_CK(cudaMemcpyAsync(c.dst, c.src, c.bytes, out_kind, st));
+    }
+    if (!plan->h_word) TV_CK(cudaMallocHost((void **)&plan->h_word, sizeof(double)));
+    TV_CK(cudaMemcpyAsync(plan->h_word, sl.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    TV_CK(cudaStreamSynchronize(st));
+    unsigned status;
+    std::memcpy(&status, plan->h_word, sizeof status);
+    if (status & kStatusNonFinite) return fail(TVSPEC_ECUDA, "non-finite value in the flow");
+    if (k_end == r.K) plan->decompositions++;
+    return TVSPEC_OK;
+}
+
 tvspec_status tvspec_rof_step(tvspec_plan *plan, const float *g, int H, int W, double lambda,
                               int n_iter, float *p1, float *p2, float *u, int mem_kind,
                               void *stream) {
