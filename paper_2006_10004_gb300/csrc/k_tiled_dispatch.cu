@@ -1,4 +1,6 @@
 // Shape table and launcher of the tiled dual-iteration kernel.
+#include <atomic>
+
 #include "k_tiled.cuh"
 
 namespace tvspec {
@@ -35,12 +37,14 @@ static TiledKernel table_kernel(int shape, int p_storage, bool fast) {
 
 int tiled_ctas_per_sm(int shape, int p_storage, bool fast, bool one) {
     constexpr int kMaxShapes = 64;
-    static int cache[kMaxShapes][4][2][2];  // 0 = not asked yet
+    // 0 = not asked yet; plans on several threads may fill an entry at once (same value)
+    static std::atomic<int> cache[kMaxShapes][4][2][2];
     if (shape < 0 || shape >= tiled_shape_count() || shape >= kMaxShapes || p_storage < 0 ||
         p_storage > 3)
         return 1;
-    int &c = cache[shape][p_storage][fast ? 1 : 0][one ? 1 : 0];
-    if (c == 0) {
+    std::atomic<int> &c = cache[shape][p_storage][fast ? 1 : 0][one ? 1 : 0];
+    int v = c.load(std::memory_order_relaxed);
+    if (v == 0) {
         int n = 0;
         const int threads = 32 * kShapes[shape].RW;
         cudaError_t e = (one && p_storage == 0)
@@ -50,9 +54,10 @@ int tiled_ctas_per_sm(int shape, int p_storage, bool fast, bool one) {
             cudaGetLastError();
             n = 1;
         }
-        c = n > 0 ? n : 1;
+        v = n > 0 ? n : 1;
+        c.store(v, std::memory_order_relaxed);
     }
-    return c;
+    return v;
 }
 
 cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *tiles, int n_tiles,
