@@ -20,7 +20,7 @@
  *     substituted into Eq. finite_inverse_trafo; h_r weighs the residual)
  *   - a Parseval-type spectrum <phi(t), f>                                    (Sec. 2.1 names it)
  *
- * Readings of points the paper leaves open (each one is listed in the design notes):
+ * Readings of points the paper leaves open:
  *   - forward differences with a zero last row/column (Neumann), divergence = -grad^T;
  *   - K ROF steps give u_0..u_K; phi_k = t_k (u_{k+1} - 2u_k + u_{k-1}) / dt^2 for k=1..K-1,
  *     t_k = k dt; S has K-1 entries;
