@@ -48,7 +48,7 @@ typedef enum {
     TVSPEC_ETIMEOUT = 4,    /* a bounded wait ran out (tvspec_wait, or a device-side spin limit) */
     TVSPEC_ENOTREADY = 5,   /* tvspec_poll: the request is still queued or running */
     TVSPEC_ECANCELLED = 6,  /* the request was cancelled before it finished */
-    TVSPEC_ENOTSUP = 7      /* the combination of options is not supported by this build */
+    TVSPEC_ENOTSUP = 7      /* the combination of options is not supported by this library */
 } tvspec_status;
 
 /* Storage type of the dual field p between kernel launches (config.p_storage). SNORM16 stores
@@ -382,7 +382,7 @@ tvspec_status tvspec_decompose_noalloc(const float *f, int H, int W, double dt, 
                                        int n_inner, const double *band_edges, int n_edges,
                                        float *bands, float *residual, double *S, void *stream);
 
-/* Number of tile shapes this build provides for TVSPEC_KERNEL_TILED, and the geometry of
+/* Number of tile shapes this library provides for TVSPEC_KERNEL_TILED, and the geometry of
  * shape `index`: columns per lane, rows per thread, warps per block, maximum iterations per
  * launch. Returns EINVAL for an index out of range. */
 int tvspec_tile_count(void);
