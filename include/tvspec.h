@@ -114,6 +114,12 @@ typedef struct {
                                n-th batch-workspace allocation (counted from 1 over the plan's
                                life) fail once with TVSPEC_ENOMEM, as if the device were out of
                                memory; default 0 (off) */
+    int test_guard_bytes;   /* write checks for tests (compute-sanitizer stands in): n > 0 puts a
+                               guard region of n bytes (rounded up to 256) before and after
+                               every array of each image's workspace, filled with a known
+                               pattern, and checks every guard after each decomposition (plain,
+                               batched, stepped, served); a guard byte found changed fails the
+                               call with TVSPEC_ECUDA naming its offset. Default 0 (off). */
 } tvspec_config;
 
 /* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in

@@ -105,18 +105,25 @@ tvspec_status make_job(const tvspec_request &req, Job *out) {
 struct SlotLayout {
     size_t band, fH, fres, f, p1, p2, q1, q2, gl, acc, facc, filt, bands, partials, ctr, ua, ub,
         u3, res, S, tr, spar, ppar, zero_begin, zero_end, total;
+    std::vector<std::pair<size_t, size_t>> guards;  // (offset, bytes) between and around arrays
 };
 
+// guard > 0 (test_guard_bytes, a multiple of 256): a guard region before the first array and
+// after every array (its alignment slack plus `guard` bytes), for the write checks of
+// slot_check_guards.
 static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naive, bool trace,
-                             int nf = 0, bool par = false) {
+                             int nf = 0, bool par = false, size_t guard = 0) {
     SlotLayout L{};
     const size_t N = (size_t)H * W;
     const int pitch = pitch_for(W);
     const size_t pb = (size_t)H * pitch * storage_bytes(storage);
-    size_t off = 0;
+    size_t off = guard;
+    if (guard) L.guards.push_back({0, guard});
     auto take = [&](size_t bytes) {
         const size_t o = off;
-        off = a256(off + std::max<size_t>(bytes, 1));
+        const size_t end = o + std::max<size_t>(bytes, 1);
+        off = a256(end) + guard;
+        if (guard) L.guards.push_back({end, off - end});
         return o;
     };
     L.band = take(K);
@@ -148,19 +155,22 @@ static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naiv
     return L;
 }
 
-size_t slot_bytes_for(const Job &j, int storage, bool naive) {
+static size_t guard_bytes(int g) { return g > 0 ? ((size_t)g + 255) / 256 * 256 : 0; }
+
+size_t slot_bytes_for(const Job &j, int storage, bool naive, int guard) {
     return layout_for(j.r.H, j.r.W, j.r.K, j.r.n_edges - 1, storage, naive, j.r.u_trace != nullptr,
-                      j.r.n_filters, j.r.S_parseval != nullptr)
+                      j.r.n_filters, j.r.S_parseval != nullptr, guard_bytes(guard))
         .total;
 }
 
 tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStream_t st,
-                         bool async_alloc, int acc_mode) {
+                         bool async_alloc, int acc_mode, int guard) {
     const tvspec_request &r = j.r;
     const bool trace = r.u_trace != nullptr;
     const int nb = r.n_edges - 1;
     const bool par = r.S_parseval != nullptr;
-    const SlotLayout L = layout_for(r.H, r.W, r.K, nb, storage, naive, trace, r.n_filters, par);
+    const SlotLayout L = layout_for(r.H, r.W, r.K, nb, storage, naive, trace, r.n_filters, par,
+                                    guard_bytes(guard));
     char *base = nullptr;
     cudaError_t e = async_alloc ? cudaMallocAsync((void **)&base, L.total, st)
                                 : cudaMalloc((void **)&base, L.total);
@@ -212,7 +222,19 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
     x.partials_par = par ? (double *)(base + L.ppar) : nullptr;
     x.ep_blocks = ep_blocks_for(r.H, r.W);
     x.p_bytes = (size_t)r.H * x.pitch * storage_bytes(storage);
-    e = cudaMemcpyAsync(x.band_of_k, j.band_of_k.data(), r.K, cudaMemcpyHostToDevice, st);
+    x.guards = L.guards;
+    e = cudaSuccess;
+    if (!L.guards.empty()) {
+        // guards inside the region cleared per decomposition must stay zero, the others keep
+        // kGuardByte; the whole cleared region starts at zero (the resident kernel clears
+        // only what it uses)
+        for (const auto &g : L.guards)
+            if (e == cudaSuccess && !(g.first >= L.zero_begin && g.first < L.zero_end))
+                e = cudaMemsetAsync(base + g.first, kGuardByte, g.second, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(base + L.zero_begin, 0, L.zero_end - L.zero_begin, st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(x.band_of_k, j.band_of_k.data(), r.K, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && r.n_filters > 0)
         e = cudaMemcpyAsync(x.filt_H, j.filt_H.data(), j.filt_H.size() * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && r.n_filters > 0)
@@ -222,6 +244,30 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
         return fail_cuda(e, "band table upload");
     }
     *s = x;
+    return TVSPEC_OK;
+}
+
+tvspec_status slot_check_guards(const Slot &s, cudaStream_t st) {
+    if (s.guards.empty() || !s.base) return TVSPEC_OK;
+    size_t total = 0;
+    for (const auto &g : s.guards) total += g.second;
+    std::vector<unsigned char> h(total);
+    size_t o = 0;
+    for (const auto &g : s.guards) {
+        TV_CK(cudaMemcpyAsync(h.data() + o, s.base + g.first, g.second, cudaMemcpyDeviceToHost, st));
+        o += g.second;
+    }
+    TV_CK(cudaStreamSynchronize(st));
+    o = 0;
+    for (const auto &g : s.guards) {
+        const bool zeroed = g.first >= s.zero_off && g.first < s.zero_off + s.zero_bytes;
+        const unsigned char want = zeroed ? 0 : kGuardByte;
+        for (size_t i = 0; i < g.second; ++i)
+            if (h[o + i] != want)
+                return fail(TVSPEC_ECUDA, "workspace guard overwritten at byte " +
+                                              std::to_string(g.first + i) + " of an image's workspace");
+        o += g.second;
+    }
     return TVSPEC_OK;
 }
 
@@ -803,7 +849,7 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
     // own still runs, alone)
     const bool naive_cfg = plan->cfg.kernel == TVSPEC_KERNEL_NAIVE;
     size_t need = 0;
-    for (const Job &j : jobs) need += slot_bytes_for(j, plan->cfg.p_storage, naive_cfg);
+    for (const Job &j : jobs) need += slot_bytes_for(j, plan->cfg.p_storage, naive_cfg, plan->cfg.test_guard_bytes);
     auto cached_bytes = [&]() {
         size_t b = 0;
         for (auto &e : plan->cache)
@@ -852,7 +898,7 @@ tvspec_status get_entry(tvspec_plan *plan, const std::vector<Job> &jobs, CacheEn
             st = fail(TVSPEC_ENOMEM, "injected workspace allocation failure (test_fail_alloc)");
         else
             st = slot_alloc(&s, jobs[E->order[i]], plan->cfg.p_storage, naive, plan->stream, false,
-                            plan->cfg.acc_mode);
+                            plan->cfg.acc_mode, plan->cfg.test_guard_bytes);
         if (st == TVSPEC_ENOMEM && !plan->cache.empty()) {
             // out of device memory with other workspaces cached: drop them all, start over
             free_entry(*E, plan->stream);
@@ -1067,6 +1113,11 @@ static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStr
         TV_CK(cudaStreamWaitEvent(plan->stream, ev, 0));
         cudaEventDestroy(ev);
     }
+    if (plan->cfg.test_guard_bytes > 0)
+        for (const Slot &sl : E->slots) {
+            s = slot_check_guards(sl, st);
+            if (s != TVSPEC_OK) return s;
+        }
     if (mk == TVSPEC_MEM_HOST) {
         TV_CK(cudaStreamSynchronize(st));
         for (int i = 0; i < n; ++i) {
@@ -1213,6 +1264,7 @@ void tvspec_config_init(tvspec_config *cfg) {
     cfg->barrier_timeout_ms = 2000;
     cfg->test_barrier_noshow = -1;
     cfg->test_fail_alloc = 0;
+    cfg->test_guard_bytes = 0;
     cfg->resident = 1;
     cfg->resident_variant = -1;
 }
@@ -1382,7 +1434,8 @@ size_t tvspec_checkpoint_bytes(tvspec_plan *plan, const tvspec_request *req) {
     Job j;
     if (make_job(*req, &j) != TVSPEC_OK) return 0;
     return sizeof(CheckpointHeader) +
-           slot_bytes_for(j, plan->cfg.p_storage, plan->cfg.kernel == TVSPEC_KERNEL_NAIVE);
+           slot_bytes_for(j, plan->cfg.p_storage, plan->cfg.kernel == TVSPEC_KERNEL_NAIVE,
+                          plan->cfg.test_guard_bytes);
 }
 
 tvspec_status tvspec_decompose_steps(tvspec_plan *plan, const tvspec_request *req, int k_begin,
@@ -1473,6 +1526,10 @@ tvspec_status tvspec_decompose_steps(tvspec_plan *plan, const tvspec_request *re
                                 {sl.S_par, r.S_parseval, r.S_parseval ? (size_t)(r.K - 1) * 8 : 0}};
         for (const CopyItem &c : out)
             if (c.bytes) TV_CK(cudaMemcpyAsync(c.dst, c.src, c.bytes, out_kind, st));
+    }
+    if (plan->cfg.test_guard_bytes > 0) {
+        s = slot_check_guards(sl, st);
+        if (s != TVSPEC_OK) return s;
     }
     if (!plan->h_word) TV_CK(cudaMallocHost((void **)&plan->h_word, sizeof(double)));
     TV_CK(cudaMemcpyAsync(plan->h_word, sl.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

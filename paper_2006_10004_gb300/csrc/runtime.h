@@ -72,10 +72,16 @@ struct Slot {
     int acc_mode = 0;  // epilogue arithmetic (tvspec_config::acc_mode)
     int ep_blocks = 0;
     size_t p_bytes = 0;  // bytes of one pitched p array (one component, one copy)
+    std::vector<std::pair<size_t, size_t>> guards;  // test_guard_bytes regions (offset, bytes)
 };
-size_t slot_bytes_for(const Job &j, int storage, bool naive);
+constexpr unsigned char kGuardByte = 0xA5;
+size_t slot_bytes_for(const Job &j, int storage, bool naive, int guard = 0);
 tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStream_t st,
-                         bool async_alloc, int acc_mode = 0);
+                         bool async_alloc, int acc_mode = 0, int guard = 0);
+// test_guard_bytes: every guard region of the slot still holds what it was given (zero inside
+// the region cleared per decomposition, kGuardByte elsewhere); ECUDA naming the first byte
+// written otherwise. Synchronises st.
+tvspec_status slot_check_guards(const Slot &s, cudaStream_t st);
 void slot_free(Slot *s, cudaStream_t st);
 ImgDesc slot_desc(const Slot &s, int s0);
 

@@ -126,6 +126,10 @@ static tvspec_status copy_out(cudaStream_t cst, ServeReq &r) {
     unsigned status = 0;
     TV_CK(cudaMemcpyAsync(&status, r.slot.status, sizeof(unsigned), cudaMemcpyDeviceToHost, cst));
     TV_CK(cudaStreamSynchronize(cst));
+    if (!r.slot.guards.empty()) {
+        tvspec_status g = slot_check_guards(r.slot, cst);
+        if (g != TVSPEC_OK) return g;
+    }
     if (status & kStatusBarrierTimeout)
         return fail(TVSPEC_ETIMEOUT, "a grid barrier wait ran out (a CTA did not arrive)");
     if (status & kStatusNonFinite) return fail(TVSPEC_ECUDA, "non-finite value in the flow");
@@ -215,7 +219,8 @@ void Server::loop() {
         // admission: workspace, image upload
         std::vector<std::shared_ptr<ServeReq>> started;
         for (auto &r : admitted) {
-            tvspec_status s = slot_alloc(&r->slot, r->job, c.p_storage, false, st, true, c.acc_mode);
+            tvspec_status s = slot_alloc(&r->slot, r->job, c.p_storage, false, st, true, c.acc_mode,
+                                         c.test_guard_bytes);
             if (s == TVSPEC_OK) {
                 cudaError_t e = cudaMemsetAsync(r->slot.base + r->slot.zero_off, 0, r->slot.zero_bytes, st);
                 if (e == cudaSuccess)
@@ -396,7 +401,7 @@ tvspec_status tvspec_submit(tvspec_plan *plan, const tvspec_request *req, uint64
     auto r = std::make_shared<ServeReq>();
     tvspec_status s = make_job(*req, &r->job);
     if (s != TVSPEC_OK) return s;
-    r->bytes = slot_bytes_for(r->job, plan->cfg.p_storage, false);
+    r->bytes = slot_bytes_for(r->job, plan->cfg.p_storage, false, plan->cfg.test_guard_bytes);
     Server *S = nullptr;
     s = get_server(plan, &S);
     if (s != TVSPEC_OK) return s;
