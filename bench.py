@@ -234,7 +234,7 @@ def run_gb300(args):
     if args.workload == "training":
         return run_training(args, tv, torch, local, ws)
     wl = _workload(args.workload)
-    plan = tv.Plan(local, acc_mode=args.acc_mode,
+    plan = tv.Plan(local, acc_mode=args.acc_mode, tma=1 if args.tma else 0,
                    **({"kernel": tv.KERNEL_TILED, "tile": args.tile} if args.tile >= 0 else {}))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
@@ -791,7 +791,8 @@ def run_kernel_only(args, tv, torch, local):
     torch.cuda.set_stream(stream)
     n = args.size
     f = syn.make_image(n, n, max(1, int(40 * n * n / 512 ** 2)), (2.0, 60.0), (0.05, 1.0), 0.02, 1000)
-    plan = tv.Plan(local, **({"kernel": tv.KERNEL_TILED, "tile": args.tile} if args.tile >= 0 else {}))
+    plan = tv.Plan(local, tma=1 if args.tma else 0,
+                   **({"kernel": tv.KERNEL_TILED, "tile": args.tile} if args.tile >= 0 else {}))
     pitch = tv.pitch_for(n)
     gl = torch.zeros((n, pitch), dtype=torch.float32, device=dev)
     gl[:, :n] = torch.from_numpy(f / 0.5).to(dev)
@@ -845,6 +846,8 @@ def main():
                     help="time only the dual-iteration kernel on a --size x --size image")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--launches", type=int, default=6)
+    ap.add_argument("--tma", action="store_true",
+                    help="tile loads by the tensor memory accelerator (config tma = 1)")
     ap.add_argument("--tile", type=int, default=-1,
                     help="fixed tile shape of the dual-iteration kernel (-1 = autotune), e.g. to pin the "
                          "autotuner's choice under a profiler")

@@ -120,6 +120,14 @@ typedef struct {
                                pattern, and checks every guard after each decomposition (plain,
                                batched, stepped, served); a guard byte found changed fails the
                                call with TVSPEC_ECUDA naming its offset. Default 0 (off). */
+    int tma;                /* 1: single-image dual-iteration launches load their tiles with the
+                               tensor memory accelerator (three 2-D TMA copies into shared
+                               memory per CTA, completing on an mbarrier whose wait is bounded:
+                               a wait that runs out fails the call with TVSPEC_ETIMEOUT) for
+                               the tile shapes that allow it (float32 p, 16-byte aligned tile
+                               columns, tile in static shared memory: shapes 8, 24, 25); other
+                               shapes and batches keep per-thread loads. Same bits either way.
+                               0 (default): per-thread loads. */
 } tvspec_config;
 
 /* One decomposition. Every pointer is in host memory when mem_kind == TVSPEC_MEM_HOST and in

@@ -49,7 +49,7 @@ class Config(ctypes.Structure):
                 ("test_barrier_noshow", ctypes.c_int), ("resident", ctypes.c_int),
                 ("resident_variant", ctypes.c_int), ("acc_mode", ctypes.c_int),
                 ("tune_cache", ctypes.c_char_p), ("test_fail_alloc", ctypes.c_int),
-                ("test_guard_bytes", ctypes.c_int)]
+                ("test_guard_bytes", ctypes.c_int), ("tma", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):

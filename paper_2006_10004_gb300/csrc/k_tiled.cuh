@@ -21,10 +21,19 @@
 // touch a border skip all masks.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (a plain struct; no driver call in device code)
+
 #include "chambolle_math.cuh"
 #include "tvspec_internal.h"
 
 namespace tvspec {
+
+// Tensor maps of the tile loads by the tensor memory accelerator (option `tma`): the copy of
+// p1 / p2 the launch reads, and g/lambda; 2-D float32 [H][W] with row stride pitch, box = the
+// CTA's tile, zero fill outside the image.
+struct TmaMaps {
+    CUtensorMap p1, p2, gl;
+};
 
 template <typename P, int V>
 struct alignas(sizeof(P) * V) PPack {
@@ -137,10 +146,77 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
     }
 }
 
-// One CTA's work on tile (tx, ty) of image d: load, iterate, store the centre.
-template <int V, int R, int RW, int TB, typename P, bool FAST>
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// The tile of p1, p2 and g/lambda at (xs, ys) into shared memory by three TMA copies (issued by
+// one thread, completing on one mbarrier), then each thread's own pixels into its registers:
+// the values the per-thread loads give (the maps read zeros outside the image, as those loads
+// substitute). The wait is bounded: if any thread runs out, the CTA sets kStatusCopyTimeout
+// and returns false (uniformly), and the host reports the call as timed out.
+constexpr long kTmaSpinLimit = 1l << 22;
+
+template <int V, int R, int RW>
+__device__ __forceinline__ bool tma_tile_load(const TmaMaps &tm, int xs, int ys, unsigned *status,
+                                              float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
+                                              float2 (&gl)[R][V / 2], int lane, int wy) {
+    constexpr int VP = V / 2;
+    constexpr int TW = 32 * V;
+    constexpr int TH = RW * R;
+    __shared__ __align__(128) float s_tile[3][TH][TW];
+    __shared__ __align__(8) unsigned long long s_bar;
+    const uint32_t bar = smem_addr(&s_bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((unsigned)(3 * TH * TW * sizeof(float)))
+                     : "memory");
+        const CUtensorMap *maps[3] = {&tm.p1, &tm.p2, &tm.gl};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(&s_tile[a][0][0])),
+                "l"(reinterpret_cast<uint64_t>(maps[a])), "r"(xs), "r"(ys), "r"(bar)
+                : "memory");
+    }
+    uint32_t done = 0;
+    for (long it = 0; it < kTmaSpinLimit && !done; ++it)
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    if (__syncthreads_or(!done)) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusCopyTimeout);
+        return false;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = wy * R + r;
+        const FPack<V> a = *reinterpret_cast<const FPack<V> *>(&s_tile[0][row][lane * V]);
+        const FPack<V> b = *reinterpret_cast<const FPack<V> *>(&s_tile[1][row][lane * V]);
+        const FPack<V> c = *reinterpret_cast<const FPack<V> *>(&s_tile[2][row][lane * V]);
+#pragma unroll
+        for (int j = 0; j < VP; ++j) {
+            p1[r][j] = make_float2(a.v[2 * j], a.v[2 * j + 1]);
+            p2[r][j] = make_float2(b.v[2 * j], b.v[2 * j + 1]);
+            gl[r][j] = make_float2(c.v[2 * j], c.v[2 * j + 1]);
+        }
+    }
+    return true;
+}
+
+// One CTA's work on tile (tx, ty) of image d: load, iterate, store the centre. TMA: the tile
+// is loaded by tma_tile_load from the maps tm (float32 p only).
+template <int V, int R, int RW, int TB, typename P, bool FAST, bool TMA = false>
 __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int gstep, int blk,
-                                           int depth, float tau) {
+                                           int depth, float tau, const TmaMaps *tm = nullptr) {
     static_assert(R * V <= 32, "mask bits");
     static_assert(V % 2 == 0, "pixels are processed in pairs");
     constexpr int VP = V / 2;
@@ -175,23 +251,28 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
     const bool col_ok = (cx >= 0) && (cx < pitch);
 
     float2 p1[R][VP], p2[R][VP], gl[R][VP];
+    if constexpr (TMA) {
+        static_assert(sizeof(P) == 4, "TMA tile loads read float32 p");
+        if (!tma_tile_load<V, R, RW>(*tm, xs, ys, d.status, p1, p2, gl, lane, wy)) return;
+    } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int y = ry + r;
-        if (col_ok && y >= 0 && y < H) {
-            const size_t off = (size_t)y * pitch + cx;
-            PPack<P, V> a = *reinterpret_cast<const PPack<P, V> *>(gp1 + off);
-            PPack<P, V> b = *reinterpret_cast<const PPack<P, V> *>(gp2 + off);
-            FPack<V> c = *reinterpret_cast<const FPack<V> *>(ggl + off);
+        for (int r = 0; r < R; ++r) {
+            const int y = ry + r;
+            if (col_ok && y >= 0 && y < H) {
+                const size_t off = (size_t)y * pitch + cx;
+                PPack<P, V> a = *reinterpret_cast<const PPack<P, V> *>(gp1 + off);
+                PPack<P, V> b = *reinterpret_cast<const PPack<P, V> *>(gp2 + off);
+                FPack<V> c = *reinterpret_cast<const FPack<V> *>(ggl + off);
 #pragma unroll
-            for (int j = 0; j < VP; ++j) {
-                p1[r][j] = make_float2(PStore<P>::load(a.v[2 * j]), PStore<P>::load(a.v[2 * j + 1]));
-                p2[r][j] = make_float2(PStore<P>::load(b.v[2 * j]), PStore<P>::load(b.v[2 * j + 1]));
-                gl[r][j] = make_float2(c.v[2 * j], c.v[2 * j + 1]);
+                for (int j = 0; j < VP; ++j) {
+                    p1[r][j] = make_float2(PStore<P>::load(a.v[2 * j]), PStore<P>::load(a.v[2 * j + 1]));
+                    p2[r][j] = make_float2(PStore<P>::load(b.v[2 * j]), PStore<P>::load(b.v[2 * j + 1]));
+                    gl[r][j] = make_float2(c.v[2 * j], c.v[2 * j + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < VP; ++j) p1[r][j] = p2[r][j] = gl[r][j] = make_float2(0.0f, 0.0f);
             }
-        } else {
-#pragma unroll
-            for (int j = 0; j < VP; ++j) p1[r][j] = p2[r][j] = gl[r][j] = make_float2(0.0f, 0.0f);
         }
     }
     if (RW > 1) {
@@ -273,6 +354,17 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     tiled_tile<V, R, RW, TB, P, FAST>(d, b % ntx, b / ntx, gstep, blk, depth, tau);
 }
 
+// Single-image form with TMA tile loads (option `tma`; the shapes tma_shape_ok accepts).
+template <int V, int R, int RW, int TB, int MINB, bool FAST>
+__global__ void __launch_bounds__(32 * RW, MINB)
+    k_tiled_one_tma(const __grid_constant__ ImgDesc d, int ntx, int gstep, int blk, int depth,
+                    float tau, const __grid_constant__ TmaMaps tm) {
+    pdl_wait();
+    pdl_trigger();
+    const int b = blockIdx.x;
+    tiled_tile<V, R, RW, TB, float, FAST, true>(d, b % ntx, b / ntx, gstep, blk, depth, tau, &tm);
+}
+
 // Shape list: index (tile-shape id of the C ABI), columns per lane V, rows per thread R, warps
 // RW, most iterations per launch TB, and the minimum CTAs per SM the register budget aims at
 // (0: left to the compiler).
@@ -308,5 +400,6 @@ __global__ void __launch_bounds__(32 * RW, MINB)
 
 using TiledKernel = void (*)(const TileRef *, const ImgDesc *, int, int, int, float);
 using TiledOneKernel = void (*)(const ImgDesc, int, int, int, int, float);
+using TiledOneTmaKernel = void (*)(const ImgDesc, int, int, int, int, float, const TmaMaps);
 
 }  // namespace tvspec

@@ -532,7 +532,7 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
     std::sort(dims.begin(), dims.end());
     std::ostringstream key;
     key << c.p_storage << '/' << c.fast_math << '/' << c.temporal_block << '/' << (one ? 1 : 0)
-        << '/' << c.pdl << '/' << c.tile;
+        << '/' << c.pdl << '/' << c.tile << '/' << (one && c.tma ? 1 : 0);
     for (auto &d : dims) key << ';' << d.first << 'x' << d.second;
     auto it = plan->tune.find(key.str());
     if (it != plan->tune.end()) {
@@ -591,7 +591,7 @@ tvspec_status choose_tiles(tvspec_plan *plan, const std::vector<Slot *> &slots, 
         cudaError_t le = cudaSuccess;
         for (int r = 0; r < kReps && le == cudaSuccess; ++r)
             le = one ? launch_tiled_one(x.shape, c.p_storage, c.fast_math != 0, x.ls.h_descs[0], 0, r,
-                                        x.depth, c.tau, st, x.pdl)
+                                        x.depth, c.tau, st, x.pdl, c.tma != 0)
                      : launch_tiled(x.shape, c.p_storage, c.fast_math != 0, x.ls.d_tiles, nt,
                                     x.ls.d_descs, 0, r, x.depth, c.tau, st, x.pdl);
         cudaGraph_t g = nullptr;
@@ -682,7 +682,7 @@ static tvspec_status enqueue_iterations(tvspec_plan *plan, LaunchSet &ls,
     for (int b = 0; b < nblk; ++b) {
         cudaError_t e = one ? launch_tiled_one(ls.shape, c.p_storage, c.fast_math != 0,
                                                ls.h_descs[0], gstep, b, ls.depth, c.tau, st,
-                                               ls.pdl)
+                                               ls.pdl, c.tma != 0)
                             : launch_tiled(ls.shape, c.p_storage, c.fast_math != 0, ls.d_tiles,
                                            nt, ls.d_descs, gstep, b, ls.depth, c.tau, st,
                                            ls.pdl);
@@ -1123,6 +1123,8 @@ static tvspec_status run_jobs(tvspec_plan *plan, std::vector<Job> &jobs, cudaStr
         for (int i = 0; i < n; ++i) {
             if (E->h_status[i] & kStatusBarrierTimeout)
                 return fail(TVSPEC_ETIMEOUT, "a grid barrier wait ran out (a CTA did not arrive)");
+            if (E->h_status[i] & kStatusCopyTimeout)
+                return fail(TVSPEC_ETIMEOUT, "a wait for a tile's TMA copies ran out");
             if (E->h_status[i] & kStatusNonFinite)
                 return fail(TVSPEC_ECUDA, "non-finite value in the flow");
         }
@@ -1265,6 +1267,7 @@ void tvspec_config_init(tvspec_config *cfg) {
     cfg->test_barrier_noshow = -1;
     cfg->test_fail_alloc = 0;
     cfg->test_guard_bytes = 0;
+    cfg->tma = 0;
     cfg->resident = 1;
     cfg->resident_variant = -1;
 }
@@ -1536,6 +1539,7 @@ tvspec_status tvspec_decompose_steps(tvspec_plan *plan, const tvspec_request *re
     TV_CK(cudaStreamSynchronize(st));
     unsigned status;
     std::memcpy(&status, plan->h_word, sizeof status);
+    if (status & kStatusCopyTimeout) return fail(TVSPEC_ETIMEOUT, "a wait for a tile's TMA copies ran out");
     if (status & kStatusNonFinite) return fail(TVSPEC_ECUDA, "non-finite value in the flow");
     if (k_end == r.K) plan->decompositions++;
     return TVSPEC_OK;

@@ -132,6 +132,7 @@ static tvspec_status copy_out(cudaStream_t cst, ServeReq &r) {
     }
     if (status & kStatusBarrierTimeout)
         return fail(TVSPEC_ETIMEOUT, "a grid barrier wait ran out (a CTA did not arrive)");
+    if (status & kStatusCopyTimeout) return fail(TVSPEC_ETIMEOUT, "a wait for a tile's TMA copies ran out");
     if (status & kStatusNonFinite) return fail(TVSPEC_ECUDA, "non-finite value in the flow");
     return TVSPEC_OK;
 }

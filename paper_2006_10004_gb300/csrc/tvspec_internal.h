@@ -15,6 +15,7 @@ constexpr int kEpBlock = 256;
 // Device status bits written by kernels into ImgDesc::status.
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusBarrierTimeout = 2u;  // a bounded grid-barrier wait ran out
+constexpr unsigned kStatusCopyTimeout = 4u;     // a bounded wait for a tile's TMA copies ran out
 
 // One image of a launch set. Lives in device memory; kernels read it, the epilogue updates
 // the per-image counter and status word.
@@ -127,8 +128,13 @@ cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *til
 bool tiled_one_available(int p_storage);
 // CTAs of the tiled kernel of a shape that fit on one SM (occupancy, asked once per kernel).
 int tiled_ctas_per_sm(int shape, int p_storage, bool fast, bool one);
+// tma: load the tile with the tensor memory accelerator where the shape allows it
+// (tma_shape_ok: float32 p, the tile's first column 16-byte aligned for every tile, the tile in
+// static shared memory); other shapes ignore it.
 cudaError_t launch_tiled_one(int shape, int p_storage, bool fast, const ImgDesc &d, int gstep,
-                             int blk, int depth, float tau, cudaStream_t st, bool pdl = false);
+                             int blk, int depth, float tau, cudaStream_t st, bool pdl = false,
+                             bool tma = false);
+bool tma_shape_ok(int shape, int p_storage);
 
 // Persistent form: all of a step's dual iterations for one image in one cooperative launch
 // (fp32 storage). step_coop_fits says whether all tiles can be resident at once.

@@ -54,7 +54,7 @@ def test_config_layout_and_defaults_match_the_header():
     want = dict(p_storage=0, warm_start=1, kernel=0, tile=-1, temporal_block=0, use_graphs=1,
                 fast_math=1, mem_budget_bytes=0, max_batch=0, pdl=1, persistent=0,
                 barrier_timeout_ms=2000, test_barrier_noshow=-1, resident=1, resident_variant=-1,
-                acc_mode=0, tune_cache=None, test_fail_alloc=0, test_guard_bytes=0)
+                acc_mode=0, tune_cache=None, test_fail_alloc=0, test_guard_bytes=0, tma=0)
     for k, v in want.items():
         assert getattr(c, k) == v, k
     assert abs(c.tau - 0.125) < 1e-9
