@@ -462,6 +462,33 @@ def test_serving_budget_and_cancel(tv):
         assert p.poll(12345) == tv.EINVAL
 
 
+def test_slow_and_absent_clients(tv):
+    # a client that polls late gets its finished results (they were retired into its buffers
+    # meanwhile); one that never waits does not hold up the others, and closing the plan with
+    # requests queued and running cancels them without hanging; the device stays usable
+    import time
+
+    jobs = [(_img(64 + 20 * i, 80, 400 + i), 0.5, 4 + i % 3, 20, syn.DYADIC_EDGES) for i in range(6)]
+    with tv.Plan(0) as p0:
+        want = [p0.decompose(*j) for j in jobs]
+    with tv.Plan(0) as p:
+        tickets = [p.submit(*j) for j in jobs]
+        time.sleep(1.0)  # nobody waits meanwhile
+        for (t, out), w in zip(tickets[:3], want[:3]):
+            assert p.poll(t) in (tv.OK, tv.ENOTREADY)
+            assert p.wait(t, 60000) == tv.OK
+            _same(out, w)
+        # tickets[3:] are never claimed
+    with tv.Plan(0, max_batch=2) as p:
+        for _ in range(3):
+            p.submit(_img(512, 512, 41), 0.5, 50, 300, syn.DYADIC_EDGES)
+        p.submit(*jobs[0])
+        t0 = time.perf_counter()
+    assert time.perf_counter() - t0 < 60.0  # closing cancelled the queue instead of draining it
+    with tv.Plan(0) as p:
+        _same(p.decompose(*jobs[1]), want[1])
+
+
 def test_cached_batch_workspaces_stay_within_the_budget(tv):
     imgs = [_img(120 + 10 * i, 130, 60 + i) for i in range(6)]
     a = [(imgs[i], 0.5, 5, 20, syn.DYADIC_EDGES) for i in range(3)]
