@@ -111,8 +111,9 @@ struct SlotLayout {
 // guard > 0 (test_guard_bytes, a multiple of 256): a guard region before the first array and
 // after every array (its alignment slack plus `guard` bytes), for the write checks of
 // slot_check_guards.
-static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naive, bool trace,
-                             int nf = 0, bool par = false, size_t guard = 0) {
+static SlotLayout layout_for(int H, int W, int K, int nb, int storage,
+                             [[maybe_unused]] bool naive, bool trace, int nf = 0,
+                             bool par = false, size_t guard = 0) {
     SlotLayout L{};
     const size_t N = (size_t)H * W;
     const int pitch = pitch_for(W);
