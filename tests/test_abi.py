@@ -60,6 +60,35 @@ def test_config_layout_and_defaults_match_the_header():
     assert abs(c.tau - 0.125) < 1e-9
 
 
+def _header_fields(struct_name):
+    """Member names of a typedef'd struct of include/tvspec.h, in declaration order."""
+    text = open(os.path.join(ROOT, "include", "tvspec.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct(?: \w+)? \{([^}]*)\} " + struct_name + ";", text)
+    assert m, struct_name
+    names = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        decl = re.sub(r"\[[^]]*\]", "", decl)  # array extents
+        head, _, rest = decl.partition(",")
+        names.append(re.findall(r"(\w+)\s*$", head)[0])
+        names += [x.strip().lstrip("*").strip() for x in rest.split(",") if x.strip()]
+    return names
+
+
+@pytest.mark.parametrize("struct,binding", [("tvspec_config", "Config"), ("tvspec_request", "Request"),
+                                            ("tvspec_stats", "Stats"), ("tvspec_crop", "Crop"),
+                                            ("tvspec_training_request", "TrainingRequest"),
+                                            ("tvspec_rof_request", "RofRequest")])
+def test_binding_structs_follow_the_header(struct, binding):
+    # same members in the same order as the C declarations (the binding passes these by pointer)
+    fields = [n for n, _ in getattr(tv, binding)._fields_]
+    renamed = {"lambda": "lam"}  # a Python keyword
+    assert fields == [renamed.get(n, n) for n in _header_fields(struct)]
+
+
 def test_tile_table():
     shapes = tv.tile_shapes()
     assert len(shapes) >= 8
