@@ -32,6 +32,17 @@ def test_library_loads_and_exports_every_declared_symbol():
     assert set(tv._SIGS) == set(names)
 
 
+def test_binding_signatures_have_the_declared_arity():
+    text = open(os.path.join(ROOT, "include", "tvspec.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for name, (_, argtypes) in tv._SIGS.items():
+        m = re.search(r"\b" + name + r"\s*\(([^)]*)\)", text)
+        assert m, name
+        params = m.group(1).strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(argtypes) == n, (name, len(argtypes), n)
+
+
 def test_status_strings_and_version():
     lib = tv.load()
     for code, name in tv.STATUS.items():
