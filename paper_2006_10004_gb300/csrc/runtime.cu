@@ -1540,6 +1540,8 @@ tvspec_status tvspec_decompose_steps(tvspec_plan *plan, const tvspec_request *re
     TV_CK(cudaStreamSynchronize(st));
     unsigned status;
     std::memcpy(&status, plan->h_word, sizeof status);
+    if (status & kStatusBarrierTimeout)
+        return fail(TVSPEC_ETIMEOUT, "a grid barrier wait ran out (a CTA did not arrive)");
     if (status & kStatusCopyTimeout) return fail(TVSPEC_ETIMEOUT, "a wait for a tile's TMA copies ran out");
     if (status & kStatusNonFinite) return fail(TVSPEC_ECUDA, "non-finite value in the flow");
     if (k_end == r.K) plan->decompositions++;

@@ -355,6 +355,7 @@ static tvspec_status training_locked(tvspec_plan *plan, const tvspec_training_re
     if (rs != TVSPEC_OK) return rs;
     for (unsigned w : hstatus) {
         if (w & kStatusBarrierTimeout) return fail(TVSPEC_ETIMEOUT, "a grid barrier wait ran out");
+        if (w & kStatusCopyTimeout) return fail(TVSPEC_ETIMEOUT, "a wait for a tile's TMA copies ran out");
         if (w & kStatusNonFinite) return fail(TVSPEC_ECUDA, "non-finite value in the flow");
     }
     plan->decompositions += n;
