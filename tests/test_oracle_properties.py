@@ -1,0 +1,72 @@
+"""Randomised checks of the oracle against what the method fixes for any input (hypothesis
+draws the image size, the schedule and the image): the telescoping reconstruction of
+Eq. spectral_bands / Eq. finite_inverse_trafo, mean preservation and zero-sum phi (div has zero
+sum), S as the L1 norm of phi, exact one-homogeneity under (c f, c dt) with c = 2 (the dual
+iterations see g / dt unchanged), and exact transpose equivariance of u and the bands (the
+isotropic norm is symmetric; S, a sum in row-major order, up to rounding). The fixed-seed
+versions of these pins live in test_oracle_pins.py; here the sizes include 1-pixel rows and
+columns and the schedules include n_inner = 0. Derandomised: the same draws on every run."""
+import math
+
+import numpy as np
+import pytest
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import given, settings  # noqa: E402
+from hypothesis import strategies as st  # noqa: E402
+
+import oracle  # noqa: E402
+
+EDGE_SETS = ([0.0, math.inf], [0.0, 1.0, 2.0, 4.0, math.inf], [0.5, 3.0, math.inf], [0.0, 0.25, 0.75, 10.0])
+
+
+@st.composite
+def problems(draw):
+    H = draw(st.integers(1, 12))
+    W = draw(st.integers(1, 12))
+    K = draw(st.integers(2, 7))
+    n_inner = draw(st.integers(0, 25))
+    dt = draw(st.sampled_from([0.125, 0.25, 0.5, 1.0]))
+    edges = draw(st.sampled_from(EDGE_SETS))
+    seed = draw(st.integers(0, 2 ** 31 - 1))
+    rng = np.random.default_rng(seed)
+    f = (rng.standard_normal((H, W)) * draw(st.sampled_from([0.1, 1.0, 10.0]))).astype(np.float32)
+    return f, dt, K, n_inner, edges
+
+
+@settings(max_examples=60, deadline=None, derandomize=True)
+@given(problems(), st.booleans())
+def test_reconstruction_mean_and_l1(p, warm):
+    f, dt, K, n, edges = p
+    r = oracle.decompose(f, dt, K, n, edges, warm_start=warm, trace=True)
+    f64 = f.astype(np.float64)
+    scale = max(1.0, float(np.abs(f64).max()))
+    # Eq. spectral_bands + Eq. finite_inverse_trafo: bands cover [e_0, e_last); with e_0 > 0 or
+    # a finite last edge some t_k fall outside every band, so reconstruct from phi directly
+    u = r["u"]
+    phi = [(k * dt) * (u[k + 1] - 2 * u[k] + u[k - 1]) / dt ** 2 for k in range(1, K)]
+    rec = sum(p_ * dt for p_ in phi) + r["residual"] if phi else r["residual"]
+    assert np.abs(rec - f64).max() <= 1e-12 * scale
+    if edges[0] == 0.0 and math.isinf(edges[-1]):
+        assert np.abs(r["bands"].sum(0) + r["residual"] - f64).max() <= 1e-12 * scale
+    for k in range(K + 1):  # div has zero sum: the mean stays in u
+        assert abs(u[k].sum() - f64.sum()) <= 1e-12 * scale * f.size
+    for k, p_ in enumerate(phi, start=1):
+        assert abs(p_.sum()) <= 1e-9 * scale * f.size
+        assert r["S"][k - 1] == pytest.approx(np.abs(p_).sum(), rel=1e-12, abs=1e-300)
+
+
+@settings(max_examples=40, deadline=None, derandomize=True)
+@given(problems())
+def test_one_homogeneity_and_transpose_exact(p):
+    f, dt, K, n, edges = p
+    a = oracle.decompose(f, dt, K, n, edges, trace=True)
+    b = oracle.decompose(2 * f, 2 * dt, K, n, [2 * e for e in edges], trace=True)
+    assert np.array_equal(b["u"], 2 * a["u"])
+    assert np.array_equal(b["bands"], 2 * a["bands"])
+    assert np.array_equal(b["S"], a["S"])
+    t = oracle.decompose(np.ascontiguousarray(f.T), dt, K, n, edges, trace=True)
+    assert np.array_equal(t["u"], np.transpose(a["u"], (0, 2, 1)))
+    assert np.array_equal(t["bands"], np.transpose(a["bands"], (0, 2, 1)))
+    # S sums |phi| in row-major order, which the transpose permutes: equal up to rounding
+    np.testing.assert_allclose(t["S"], a["S"], rtol=1e-12, atol=0)
