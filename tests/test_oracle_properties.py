@@ -70,3 +70,22 @@ def test_one_homogeneity_and_transpose_exact(p):
     assert np.array_equal(t["bands"], np.transpose(a["bands"], (0, 2, 1)))
     # S sums |phi| in row-major order, which the transpose permutes: equal up to rounding
     np.testing.assert_allclose(t["S"], a["S"], rtol=1e-12, atol=0)
+
+
+@settings(max_examples=25, deadline=None, derandomize=True)
+@given(st.integers(2, 4), st.integers(0, 6), st.integers(0, 2 ** 31 - 1))
+def test_finite_propagation_speed(K, n, seed):
+    # an iteration moves information one pixel (w reads p one pixel up / left, the update reads
+    # w one pixel down / right, u_{k+1} reads p one pixel up / left): after K steps of n
+    # iterations an output depends only on inputs within K (n + 1) pixels, so a window with that
+    # margin reproduces the full image's outputs on its centre bit for bit (the premise of the
+    # largest-image GPU test, which compares windows)
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((80, 84)).astype(np.float32)
+    edges = [0.0, 1.0, math.inf]
+    full = oracle.decompose(f, 0.5, K, n, edges)
+    m, y0, x0, side = K * (n + 1), 35, 37, 6  # the window stays inside the image (m <= 28)
+    win = oracle.decompose(f[y0 - m:y0 + side + m, x0 - m:x0 + side + m], 0.5, K, n, edges)
+    c = (slice(None), slice(m, m + side), slice(m, m + side))
+    assert np.array_equal(win["bands"][c], full["bands"][:, y0:y0 + side, x0:x0 + side])
+    assert np.array_equal(win["residual"][c[1:]], full["residual"][y0:y0 + side, x0:x0 + side])
