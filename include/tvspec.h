@@ -23,8 +23,10 @@
  *     plan is unchanged and usable. tvspec_last_error() gives a one-line reason.
  *   - Arithmetic: the dual iterations run in float32 (p may be stored as fp16/bf16 between
  *     kernel launches, see tvspec_config.p_storage); u, phi, S, the band sums and the residual
- *     are computed in float64. Results do not depend on the tile shape, the iterations per
- *     kernel launch, the batch an image runs in, or graph versus plain launches (bit-identical).
+ *     are computed in float64 (or float-float pairs, tvspec_config.acc_mode). Results do not
+ *     depend on the tile shape, the iterations per kernel launch, the batch an image runs in,
+ *     graph versus plain launches, TMA versus per-thread tile loads, or a checkpoint / resume
+ *     in between (bit-identical).
  *   - The library never falls back to CPU arithmetic: without a usable CUDA device every
  *     compute call returns TVSPEC_ECUDA.
  */
