@@ -182,30 +182,82 @@ def _oracle_batch_sample(jobs):
     return sum(j.px_iters for j in jobs) / el / 1e6, el, oracle.max_threads()
 
 
+def _reference_line(args, ws, metric, unit, value, times, workload, sample, cores):
+    return {"impl": "reference", "metric": metric, "value": value, "unit": unit,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * np.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the only other implementation of the method) on the
+    host's cores, each step a bounded sample of the workload."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    wl = _workload(args.workload)
-    job = wl.jobs[0]
-    kk = max(2, min(job.K, args.ref_steps_k))
-    for _ in range(args.warmup):
-        _oracle_sample(job, 2)
-    times = []
-    cores = None
-    for _ in range(args.steps):
-        v, el, K, cores = _oracle_sample(job, kk)
-        times.append(el)
-    px_it = job.f.size * kk * job.n_inner
-    value = px_it * len(times) / sum(times) / 1e6
-    sample = f"first {kk} of {job.K} ROF steps of the {job.f.shape[0]}x{job.f.shape[1]} image, {job.n_inner} iterations each"
-    line = {"impl": "reference", "metric": "Chambolle Mpx*iter/s", "value": value, "unit": "Mpx*iter/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * np.mean(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl.name, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    import oracle
+
+    kk_req = max(2, args.ref_steps_k)
+    if args.workload == "training":
+        # whole decompositions (K = 50, 300 iterations) of the first 8 crops of the set
+        srcs, crops = training_workload(8)
+        run = lambda: oracle.training_set(srcs, crops, 64, 1, 0.5, 50, 300, syn.DYADIC_EDGES)
+        px_it = 8 * 64 * 64 * 50 * 300
+        for _ in range(args.warmup):
+            oracle.training_set(srcs, crops[:1], 64, 1, 0.5, 2, 300, syn.DYADIC_EDGES)
+        times = []
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            run()
+            times.append(time.perf_counter() - t)
+        value = px_it * len(times) / sum(times) / 1e6
+        sample = "8 crops of 64x64 (whole decompositions, K=50, 300 iterations) of the training set"
+        line = _reference_line(args, ws, "Chambolle Mpx*iter/s", "Mpx*iter/s", value, times,
+                               training_workload_name(args.crops), sample, oracle.max_threads())
+    elif args.workload == "config4":
+        # served images/s of the oracle one request at a time: the first kk ROF steps of each of
+        # the first 4 requests at 100 req/s, each request's time scaled to its K steps
+        _, jobs = config4_requests(config4_pool(), 100.0, 4)
+        for _ in range(args.warmup):
+            oracle.decompose(jobs[0][0][:64, :64], 0.5, 2, 300, syn.DYADIC_EDGES)
+        times = []
+        for _ in range(args.steps):
+            est = 0.0
+            for f, dt, K, n, e in jobs:
+                kk = min(K, kk_req)
+                t = time.perf_counter()
+                oracle.decompose(f, dt, kk, n, e)
+                est += (time.perf_counter() - t) * K / kk
+            times.append(est / len(jobs))
+        value = len(times) / sum(times)
+        sample = (f"first {kk_req} ROF steps of each of the first 4 requests of the 100 req/s "
+                  "stream, each request's time scaled by K / steps run; one request at a time")
+        line = _reference_line(args, ws, "served images/s", "images/s", value, times, "config4_serving",
+                               sample, oracle.max_threads())
+    else:
+        wl = _workload(args.workload)
+        # one image (config 2: the first two images of the batch), its first kk ROF steps
+        jobs = wl.jobs[:2] if args.workload == "config2" else wl.jobs[:1]
+        for _ in range(args.warmup):
+            _oracle_sample(jobs[0], 2)
+        times = []
+        px_it = 0
+        for _ in range(args.steps):
+            el = 0.0
+            px_it = 0
+            for job in jobs:
+                kk = max(2, min(job.K, kk_req))
+                _, e, _, _ = _oracle_sample(job, kk)
+                el += e
+                px_it += job.f.size * kk * job.n_inner
+            times.append(el)
+        value = px_it * len(times) / sum(times) / 1e6
+        sample = "; ".join(f"first {max(2, min(j.K, kk_req))} of {j.K} ROF steps of the "
+                           f"{j.f.shape[0]}x{j.f.shape[1]} image, {j.n_inner} iterations each" for j in jobs)
+        line = _reference_line(args, ws, "Chambolle Mpx*iter/s", "Mpx*iter/s", value, times, wl.name,
+                               sample, oracle.max_threads())
     print(json.dumps(line))
     return 0
 
@@ -585,6 +637,11 @@ def measure_batched(tv, torch, local, steps: int, warmup: int, with_clocks=None)
     return out
 
 
+def training_workload_name(n: int) -> str:
+    return (f"{n} crops 64x64 (1/3 from 128x128 downsampled by 2) of 16 sources 512x512, "
+            "standardised over the set, K=50, dt=.5, 300 iterations, 6 dyadic bands")
+
+
 def training_workload(n: int = 3000, size: int = 64, n_sources: int = 16, seed: int = 9000):
     """The paper's ground-truth generation (Sec. 4.1): n crops of size^2 from synthetic
     512^2 greyscale sources, one third of them from (2 size)^2 windows downsampled by 2;
@@ -617,8 +674,7 @@ def measure_crops(tv, torch, local, n: int = 3000, compare: bool = True, acc_mod
     stream = torch.cuda.current_stream(dev)
     srcs, crops = training_workload(n)
     srcs_d = [torch.from_numpy(x).to(dev) for x in srcs]
-    out = {"workload": f"{n} crops 64x64 (1/3 from 128x128 downsampled by 2) of 16 sources 512x512, "
-                       "standardised over the set, K=50, dt=.5, 300 iterations, 6 dyadic bands"}
+    out = {"workload": training_workload_name(n)}
 
     def timed(fn, reps=2, warm=3):
         # the untimed calls (the second one captures the graph) are still running on the
@@ -705,6 +761,27 @@ def run_batched(args, tv, torch, local, ws):
     return 0
 
 
+def config4_pool():
+    """8 synthetic images per served size (config-1 generator, shapes scaled with the area)."""
+    return {s: [syn.make_image(s, s, max(1, int(40 * s * s / 512 ** 2)), (2.0, 60.0), (0.05, 1.0), 0.02,
+                               4000 + 10 * s + k) for k in range(8)] for s in (256, 512, 1024, 2048)}
+
+
+def config4_requests(pool, rate: float, n_req: int):
+    """Poisson arrivals at `rate` req/s of requests: size 256^2..2048^2 with weights
+    .4/.3/.2/.1, K ~ U{20..50}, dt .5, 300 iterations, 6 dyadic bands (seeded by the rate)."""
+    rng = np.random.default_rng(4000 + int(rate))
+    arrivals, jobs = [], []
+    t = 0.0
+    for j in range(n_req):
+        t += float(rng.exponential(1.0 / rate))
+        s = int(rng.choice([256, 512, 1024, 2048], p=[0.4, 0.3, 0.2, 0.1]))
+        K = int(rng.integers(20, 51))
+        arrivals.append(t)
+        jobs.append((pool[s][j % 8], 0.5, K, 300, syn.DYADIC_EDGES))
+    return arrivals, jobs
+
+
 def measure_serving(tv, local, rates, n_req):
     """Config 4: Poisson arrivals of single-image requests (sizes 256^2..2048^2 with weights
     .4/.3/.2/.1, K ~ U{20..50}, dt .5, 300 iterations, 6 bands) into the serving loop
@@ -713,21 +790,10 @@ def measure_serving(tv, local, rates, n_req):
     offline batches of up to 500 (each timed on its second run: workspace, tile choice and graph
     built by the first), for images/s. A pool of 8 images per size is reused (timing does not
     depend on the picture)."""
-    pool = {}
-    for s in (256, 512, 1024, 2048):
-        pool[s] = [syn.make_image(s, s, max(1, int(40 * s * s / 512 ** 2)), (2.0, 60.0), (0.05, 1.0), 0.02,
-                                  4000 + 10 * s + k) for k in range(8)]
+    pool = config4_pool()
     points = []
     for rate in rates:
-        rng = np.random.default_rng(4000 + int(rate))
-        arrivals, jobs = [], []
-        t = 0.0
-        for j in range(n_req):
-            t += float(rng.exponential(1.0 / rate))
-            s = int(rng.choice([256, 512, 1024, 2048], p=[0.4, 0.3, 0.2, 0.1]))
-            K = int(rng.integers(20, 51))
-            arrivals.append(t)
-            jobs.append((pool[s][j % 8], 0.5, K, 300, syn.DYADIC_EDGES))
+        arrivals, jobs = config4_requests(pool, rate, n_req)
         px_it = sum(j[0].size * j[2] * j[3] for j in jobs)
         with tv.Plan(local) as plan:
             tw, _ = plan.submit(*jobs[0])  # warm the scheduler thread and its tile choice
