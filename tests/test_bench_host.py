@@ -32,3 +32,26 @@ def test_malformed_and_missing_samples():
     s = _summary(["", "garbage", "0, [N/A], 2070, 1, 0x0, a, b, c, d", _line(2050)])
     assert s["samples"] == 1 and s["sm_mhz"] == 2050.0
     assert _summary([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_reference_arm_prints_the_contract_line():
+    # `bench.py --impl reference` runs the FP64 oracle on the host: one JSON line with the
+    # fields of the bench contract (a tiny sample here: two ROF steps of the 512^2 image)
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "3", "--ref-steps-k", "2"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["config"]["workload"] == "config1_512x512_K50_it300"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
