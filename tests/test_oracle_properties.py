@@ -89,3 +89,26 @@ def test_finite_propagation_speed(K, n, seed):
     c = (slice(None), slice(m, m + side), slice(m, m + side))
     assert np.array_equal(win["bands"][c], full["bands"][:, y0:y0 + side, x0:x0 + side])
     assert np.array_equal(win["residual"][c[1:]], full["residual"][y0:y0 + side, x0:x0 + side])
+
+
+@settings(max_examples=40, deadline=None, derandomize=True)
+@given(problems(), st.integers(0, 2 ** 31 - 1))
+def test_filters_and_parseval_identities(p, seed):
+    # Eq. filteredTVtrafo in Eq. finite_inverse_trafo: the all-pass filter (H = 1, h_r = 1)
+    # reconstructs f; filtering is linear in H; and the Parseval-type spectrum splits the energy,
+    # sum_k <phi_k, f> dt + <f_r, f> = |f|^2
+    f, dt, K, n, edges = p
+    rng = np.random.default_rng(seed)
+    h1, h2 = rng.standard_normal(K - 1), rng.standard_normal(K - 1)
+    r1, r2 = float(rng.standard_normal()), float(rng.standard_normal())
+    out = oracle.decompose(f, dt, K, n, edges,
+                           filters=[(np.ones(K - 1), 1.0), (h1, r1), (h2, r2), (h1 + 2 * h2, r1 + 2 * r2)])
+    f64 = f.astype(np.float64)
+    scale = max(1.0, float(np.abs(f64).max()))
+    F = out["filtered"]
+    assert np.abs(F[0] - f64).max() <= 1e-12 * scale
+    lin_scale = scale * max(1.0, float(np.abs(np.concatenate([h1, h2, [r1, r2]])).max()))
+    assert np.abs(F[3] - (F[1] + 2 * F[2])).max() <= 1e-11 * lin_scale
+    energy = float((f64 * f64).sum())
+    total = out["S_parseval"].sum() * dt + float((out["residual"] * f64).sum())
+    assert abs(total - energy) <= 1e-10 * max(energy, scale * scale)
