@@ -112,3 +112,23 @@ def test_filters_and_parseval_identities(p, seed):
     energy = float((f64 * f64).sum())
     total = out["S_parseval"].sum() * dt + float((out["residual"] * f64).sum())
     assert abs(total - energy) <= 1e-10 * max(energy, scale * scale)
+
+
+@settings(max_examples=60, deadline=None, derandomize=True)
+@given(st.integers(1, 10), st.integers(1, 10), st.floats(0.01, 5.0), st.integers(0, 2 ** 31 - 1))
+def test_weak_duality_of_the_rof_gap(H, W, lam, seed):
+    # Eq. ROF: for any u and any dual field with |p| <= 1 the primal value
+    # 1/2 |u - g|^2 + lam J_TV(u) is at least the dual value 1/2 |g|^2 - 1/2 |g - lam div p|^2,
+    # so both gap functions are non-negative; with u = g - lam div p they coincide
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((H, W))
+    u = rng.standard_normal((H, W)) * rng.choice([0.01, 1.0, 10.0])
+    ang = rng.uniform(0, 2 * np.pi, (H, W))
+    mag = rng.uniform(0, 1, (H, W))
+    p1, p2 = mag * np.cos(ang), mag * np.sin(ang)
+    scale = 1.0 + float((g * g).sum() + (u * u).sum())
+    assert oracle.rof_gap_pair(g, lam, u, p1, p2) >= -1e-12 * scale
+    assert oracle.rof_gap(g, lam, p1, p2) >= -1e-12 * scale
+    uc, q1, q2 = oracle.chambolle(g, lam, 0, p1=p1, p2=p2)  # u = g - lam div p
+    assert oracle.rof_gap_pair(g, lam, uc, p1, p2) == pytest.approx(oracle.rof_gap(g, lam, p1, p2),
+                                                                    rel=1e-9, abs=1e-12 * scale)
