@@ -119,7 +119,8 @@ def test_filters_and_parseval_identities(p, seed):
 def test_weak_duality_of_the_rof_gap(H, W, lam, seed):
     # Eq. ROF: for any u and any dual field with |p| <= 1 the primal value
     # 1/2 |u - g|^2 + lam J_TV(u) is at least the dual value 1/2 |g|^2 - 1/2 |g - lam div p|^2,
-    # so both gap functions are non-negative; with u = g - lam div p they coincide
+    # so both gap functions are non-negative; with u = g - lam div p they coincide; at the
+    # optimum the gap is zero
     rng = np.random.default_rng(seed)
     g = rng.standard_normal((H, W))
     u = rng.standard_normal((H, W)) * rng.choice([0.01, 1.0, 10.0])
@@ -132,3 +133,8 @@ def test_weak_duality_of_the_rof_gap(H, W, lam, seed):
     uc, q1, q2 = oracle.chambolle(g, lam, 0, p1=p1, p2=p2)  # u = g - lam div p
     assert oracle.rof_gap_pair(g, lam, uc, p1, p2) == pytest.approx(oracle.rof_gap(g, lam, p1, p2),
                                                                     rel=1e-9, abs=1e-12 * scale)
+    # and the gap closes at the optimum (fast gradient projection, O(1/k^2)): strong duality
+    us, s1, s2 = oracle.fgp(g, lam, 3000)
+    gap = oracle.rof_gap_pair(g, lam, us, s1, s2)
+    gs = 1.0 + float((g * g).sum())
+    assert -1e-9 * gs <= gap <= 1e-6 * gs
