@@ -138,3 +138,30 @@ def test_weak_duality_of_the_rof_gap(H, W, lam, seed):
     gap = oracle.rof_gap_pair(g, lam, us, s1, s2)
     gs = 1.0 + float((g * g).sum())
     assert -1e-9 * gs <= gap <= 1e-6 * gs
+
+
+@settings(max_examples=60, deadline=None, derandomize=True)
+@given(st.integers(1, 8), st.integers(1, 3), st.integers(0, 2 ** 31 - 1))
+def test_crop_and_standardisation(size, scale, seed):
+    # the training-data preparation (Sec. 4.1): a crop is the scale x scale block average of
+    # its (scale size)^2 window, rounded to float32 (numpy's block mean, to one float32 ulp);
+    # standardising over the set gives mean 0 and population std 1, per image likewise
+    rng = np.random.default_rng(seed)
+    sH, sW = int(rng.integers(scale * size, scale * size + 20)), int(rng.integers(scale * size, scale * size + 20))
+    src = (rng.standard_normal((sH, sW)) * 3 + 1).astype(np.float32)
+    y = int(rng.integers(0, sH - scale * size + 1))
+    x = int(rng.integers(0, sW - scale * size + 1))
+    c = oracle.crop(src, y, x, size, scale)
+    win = src[y:y + scale * size, x:x + scale * size].astype(np.float64)
+    want = win.reshape(size, scale, size, scale).mean(axis=(1, 3)).astype(np.float32)
+    assert np.all(np.abs(c - want) <= np.spacing(np.abs(want).astype(np.float32)))
+    imgs = np.stack([oracle.crop(src, int(rng.integers(0, sH - scale * size + 1)),
+                                 int(rng.integers(0, sW - scale * size + 1)), size, scale)
+                     for _ in range(3)])
+    if np.ptp(imgs) > 0:
+        z, ms = oracle.standardize(imgs, 1)
+        assert abs(z.mean()) <= 1e-6 and abs(z.std() - 1.0) <= 1e-6
+    z2, ms2 = oracle.standardize(imgs, 2)
+    for i in range(3):
+        if np.ptp(imgs[i]) > 0:
+            assert abs(z2[i].mean()) <= 1e-6 and abs(z2[i].std() - 1.0) <= 1e-6
