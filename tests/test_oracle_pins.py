@@ -61,6 +61,44 @@ def test_two_pixel_rof_closed_form(golden_dir):
         np.testing.assert_allclose(u.ravel(), case["u"], rtol=0, atol=1e-10)
 
 
+def _frac_array(rows):
+    from fractions import Fraction
+
+    return np.array([[float(Fraction(v)) for v in row] for row in rows], dtype=np.float64)
+
+
+def test_chambolle_one_and_two_iterations_hand_derived(golden_dir):
+    # A fixed iteration count, not the converged step, is what the decomposition computes, so
+    # the iterates themselves are pinned: a slip in tau or lambda that keeps the fixed point
+    # (tau/2, a denominator 1 + tau |G|^2, w = div p - lam g, ...) changes these values.
+    from fractions import Fraction
+
+    data = json.load(open(os.path.join(golden_dir, "chambolle_iterations.json")))
+    tau = float(Fraction(data["tau"]))
+    assert tau == 0.125
+    for case in data["cases"]:
+        g = _frac_array(case["g"])
+        lam = float(Fraction(case["lam"]))
+        prev = None
+        for it in case["iterations"]:
+            exp_p1, exp_p2, exp_u = (_frac_array(it[k]) for k in ("p1", "p2", "u"))
+            u, p1, p2 = oracle.chambolle(g, lam, it["n"], tau=tau)
+            for got, exp in ((p1, exp_p1), (p2, exp_p2), (u, exp_u)):
+                np.testing.assert_allclose(got, exp, rtol=0, atol=4e-15, err_msg=case["name"])
+            # the same iterate reached from the previous one (warm start of the dual)
+            if prev is not None:
+                u2, q1, q2 = oracle.chambolle(g, lam, it["n"] - prev[0], tau=tau, p1=prev[1], p2=prev[2])
+                np.testing.assert_allclose(q1, exp_p1, rtol=0, atol=4e-15)
+                np.testing.assert_allclose(q2, exp_p2, rtol=0, atol=4e-15)
+                np.testing.assert_allclose(u2, exp_u, rtol=0, atol=4e-15)
+            prev = (it["n"], p1, p2)
+            # the transposed image gives the transposed iterate with the components swapped
+            uT, p1T, p2T = oracle.chambolle(g.T.copy(), lam, it["n"], tau=tau)
+            np.testing.assert_allclose(p1T, exp_p2.T, rtol=0, atol=4e-15)
+            np.testing.assert_allclose(p2T, exp_p1.T, rtol=0, atol=4e-15)
+            np.testing.assert_allclose(uT, exp_u.T, rtol=0, atol=4e-15)
+
+
 def test_1d_segments_closed_form(golden_dir):
     data = json.load(open(os.path.join(golden_dir, "segments_1d_rof.json")))
     for case in data["cases"]:
