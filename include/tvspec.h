@@ -375,11 +375,13 @@ tvspec_status tvspec_rof_solve(tvspec_plan *plan, tvspec_rof_request *req, void 
  * implicit synchronisation of an allocation, frameworks that own all device memory).
  *
  * f (H*W), bands ((n_edges-1)*H*W), residual (H*W) and S (K-1) are DEVICE pointers on the
- * current CUDA device, caller-owned. Every other buffer comes from one file-scope device array
- * of 48 MiB inside this library, which every GPU that loads the library holds until the
- * process exits. Arithmetic and defaults are those of a default plan (float32 dual
- * iterations, float64 epilogue, tau = 1/8, warm start), and the results equal
- * tvspec_decompose with such a plan.
+ * current CUDA device, caller-owned; a pointer that is not device (or managed) memory of the
+ * current device is rejected with TVSPEC_EINVAL before anything is enqueued. Every other
+ * buffer comes from one file-scope device array of 48 MiB inside this library, which every GPU
+ * that loads the library holds until the process exits. Arithmetic and defaults are those of a
+ * default plan (float32 dual iterations, float64 epilogue, tau = 1/8, warm start) with the same
+ * per-pixel operations, so the results are bit-identical to tvspec_decompose with such a plan.
+ * The work enqueued reads no host memory (the tables travel in kernel parameters).
  *
  * Limits: 1 <= H, W <= 2048, 2 <= K <= 4096, and the workspace (about 44 bytes per pixel plus
  * small tables) must fit the 48 MiB array -- about 1.1 megapixels, so 1024x1024 fits and
@@ -388,8 +390,9 @@ tvspec_status tvspec_rof_solve(tvspec_plan *plan, tvspec_rof_request *req, void 
  *
  * The call enqueues its work on `stream` (a cudaStream_t; NULL = the legacy default stream)
  * and returns; the outputs are valid once the stream reaches that point. It allocates nothing:
- * the first call on a device looks up the array's device address once
- * (cudaGetSymbolAddress) -- make that first call before any stream capture. Every call uses
+ * the first call on a device (and the first after that device's context was destroyed and
+ * created again) looks up the array's device address (cudaGetSymbolAddress, which may load
+ * the module) -- make that first call before any stream capture. Every call uses
  * the same array and finds the previous call's contents in it (the call clears what must
  * start at zero), so calls that overlap on the GPU race: issue them on one stream, or
  * synchronise between them. A non-finite value in f is not detected (it propagates).

@@ -625,27 +625,43 @@ class Plan:
         return {k: getattr(s, k) for k, _ in Stats._fields_}
 
 
-def decompose_noalloc(f, dt: float, K: int, n_inner: int, edges, stream=None) -> Result:
+def decompose_noalloc(f, dt: float, K: int, n_inner: int, edges, stream=None, out=None) -> Result:
     """The decomposition through tvspec_decompose_noalloc, which allocates no device memory.
 
     For callers that may not call cudaMalloc where they run (see include/tvspec.h). ``f`` is a
-    2-D float32 CUDA tensor; the outputs are allocated here by torch, outside the entry point,
-    as such a caller would pre-allocate them. Images up to about 1.1 megapixels.
+    2-D float32 CUDA tensor; the call runs with ``f``'s device current. The outputs are
+    allocated here by torch, outside the entry point, as such a caller would pre-allocate them,
+    unless ``out`` gives them (a Result / dict with float32 ``bands`` (n_edges-1, H, W) and
+    ``residual`` (H, W) and float64 ``S`` (at least max(K-1, 1)) on ``f``'s device), in which
+    case nothing is allocated here either. Images up to about 1.1 megapixels.
     """
     import torch
 
     L = load()
-    f = f.contiguous()
-    if f.dtype != torch.float32 or f.dim() != 2 or not f.is_cuda:
+    if not isinstance(f, torch.Tensor) or f.dtype != torch.float32 or f.dim() != 2 or not f.is_cuda:
         raise TypeError("f must be a 2-D float32 CUDA tensor")
+    if not f.is_contiguous():
+        raise TypeError("f must be contiguous")
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
     H, W = f.shape
-    out = Result(bands=torch.empty((len(e) - 1, H, W), dtype=torch.float32, device=f.device),
-                 residual=torch.empty((H, W), dtype=torch.float32, device=f.device),
-                 S=torch.empty((max(K - 1, 1),), dtype=torch.float64, device=f.device))
-    _check(L.tvspec_decompose_noalloc(f.data_ptr(), H, W, float(dt), int(K), int(n_inner), e.ctypes.data, len(e),
-                                      out["bands"].data_ptr(), out["residual"].data_ptr(), out["S"].data_ptr(),
-                                      _stream_ptr(stream)), "tvspec_decompose_noalloc")
+    with torch.cuda.device(f.device):
+        if out is None:
+            out = Result(bands=torch.empty((len(e) - 1, H, W), dtype=torch.float32, device=f.device),
+                         residual=torch.empty((H, W), dtype=torch.float32, device=f.device),
+                         S=torch.empty((max(K - 1, 1),), dtype=torch.float64, device=f.device))
+        else:
+            b, r, S = out["bands"], out["residual"], out["S"]
+            ok = (b.dtype == torch.float32 and tuple(b.shape) == (len(e) - 1, H, W) and b.is_contiguous()
+                  and r.dtype == torch.float32 and tuple(r.shape) == (H, W) and r.is_contiguous()
+                  and S.dtype == torch.float64 and S.dim() == 1 and S.numel() >= max(K - 1, 1)
+                  and S.is_contiguous() and all(t.device == f.device for t in (b, r, S)))
+            if not ok:
+                raise TypeError("out: bands (n_edges-1, H, W) float32, residual (H, W) float32 and "
+                                "S (>= K-1,) float64, contiguous, on f's device")
+            out = Result(bands=b, residual=r, S=S)
+        _check(L.tvspec_decompose_noalloc(f.data_ptr(), H, W, float(dt), int(K), int(n_inner), e.ctypes.data,
+                                          len(e), out["bands"].data_ptr(), out["residual"].data_ptr(),
+                                          out["S"].data_ptr(), _stream_ptr(stream)), "tvspec_decompose_noalloc")
     out["S"] = out["S"][: max(K - 1, 0)]
     return out
 
