@@ -86,14 +86,16 @@ typedef struct {
     int pdl;                /* 1 (default): programmatic dependent launch between the kernels of a
                                step (the next kernel is scheduled while the previous one drains;
                                each waits for its predecessor's results before reading them); 0 off */
-    int persistent;         /* 1: run a single image's step in one cooperative launch (tiles
-                               resident for the whole step, bounded-wait grid barriers) when all
-                               its tiles fit on the GPU at once; 0 (default): one launch per block
-                               (on GB300 graph-replayed launches are as cheap as the barriers) */
-    int barrier_timeout_ms; /* longest wait at a grid barrier before the kernel gives up and the
-                               call returns TVSPEC_ETIMEOUT; default 2000 */
+    int persistent;         /* run a single image's step in one cooperative launch when all its
+                               tiles fit on the GPU at once (tiles resident for the whole step):
+                               1 with bounded-wait grid barriers between blocks of iterations,
+                               2 with each tile waiting (bounded) only for its eight neighbours'
+                               progress flags; 0 (default): one launch per block */
+    int barrier_timeout_ms; /* longest wait at a grid barrier or for a neighbour before the kernel
+                               gives up and the call returns TVSPEC_ETIMEOUT; default 2000 */
     int test_barrier_noshow;/* fault injection for tests: this CTA of the persistent kernel skips
-                               its first barrier, so the others time out; default -1 (off) */
+                               its first barrier (persistent 1) or never publishes its progress
+                               (persistent 2), so the others time out; default -1 (off) */
     int resident;           /* images up to 64x128 or 128x64 can run their whole decomposition
                                in one CTA (one launch for all of them): 1 (default) when a call
                                holds at least 32 such images (one CTA per image needs many images

@@ -30,14 +30,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// The hardware reciprocal refined by one Newton-Raphson step, s1 = s0 + s0 (1 - x s0) (two
-// fused multiply-adds). The raw approximation's error is not zero-mean, and over thousands of
-// dual iterations it drifts p measurably; after the step the error is about an ulp.
-__device__ __forceinline__ float rcp_fast(float x) {
-    const float s0 = rcp_approx(x);
-    return __fmaf_rn(s0, __fmaf_rn(-x, s0, 1.0f), s0);
-}
-
 // w_ij = (div p)_ij - g_ij / lambda with
 //   (div p)_ij = (p1_ij - p1_{i-1,j}) + (p2_ij - p2_{i,j-1}),
 // where p1_{-1,j} = p2_{i,-1} = 0 and p1 on the last row / p2 on the last column are zero
@@ -47,15 +39,57 @@ __device__ __forceinline__ float tv_w(float p1, float p1_up, float p2, float p2_
 }
 
 // p <- (p + tau G) / (1 + tau |G|), |G| = sqrt(G1^2 + G2^2)  (isotropic; Eq. TV's pointwise
-// Euclidean norm). The division is a multiplication by the reciprocal of the denominator.
+// Euclidean norm), evaluated in float32 as an increment:
+//   a = tau G,  x = |a| = tau |G|,  s = 1 / (1 + x),  p <- p + (a - p x) s.
+// The result is the same real number; the order of the float32 roundings is what differs.
+// Forming 1 + tau|G| and p + tau G first rounds away whatever of tau|G| and tau G lies below
+// half an ulp of 1 and of p, and where |G| is small (flat regions, most of an image near
+// convergence) that loss is always in the same direction: over the tens of thousands of dual
+// iterations of a decomposition it drifts p, and the bands, far more than the rounding of p
+// itself. In the increment form the small quantities x and a - p x are rounded relative to
+// their own size, and the fixed point (a = p x) does not involve s at all: an error in the
+// reciprocal only scales the step, so the hardware approximations of the square root and the
+// reciprocal (about an ulp each) are used without refinement (a float32 model of this
+// arithmetic gives the same errors against the float64 oracle with exact and with 2-ulp
+// one-sided biased square root and reciprocal). Signs are arranged so that no negation is
+// needed: na = -a, nden = -(1 + x), ns = 1 / nden, u = p x + na = -(a - p x), and u ns is the
+// increment. For tau a power of two (1/8 by default) na is exact.
 template <bool FAST>
 __device__ __forceinline__ void tv_update(float &p1, float &p2, float G1, float G2, float tau) {
-    float n2 = __fadd_rn(__fmul_rn(G1, G1), __fmul_rn(G2, G2));
-    float nrm = FAST ? sqrt_approx(n2) : __fsqrt_rn(n2);
-    float den = __fmaf_rn(tau, nrm, 1.0f);
-    float s = FAST ? rcp_fast(den) : __frcp_rn(den);
-    p1 = __fmul_rn(__fmaf_rn(tau, G1, p1), s);
-    p2 = __fmul_rn(__fmaf_rn(tau, G2, p2), s);
+    const float na1 = __fmul_rn(-tau, G1), na2 = __fmul_rn(-tau, G2);
+    const float n2 = __fadd_rn(__fmul_rn(na1, na1), __fmul_rn(na2, na2));
+    const float x = FAST ? sqrt_approx(n2) : __fsqrt_rn(n2);
+    const float nden = __fsub_rn(-1.0f, x);
+    const float ns = FAST ? rcp_approx(nden) : __frcp_rn(nden);
+    p1 = __fmaf_rn(__fmaf_rn(p1, x, na1), ns, p1);
+    p2 = __fmaf_rn(__fmaf_rn(p2, x, na2), ns, p2);
+}
+
+// The same update with p held as an unevaluated sum hi + lo of two floats (p1 + l1, p2 + l2):
+// the increment plus the carried remainder, d = u ns + lo, is added to hi, and what of d the
+// sum could not hold stays in lo (Fast2Sum: lo = d - ((hi + d) - hi); exact when |hi| >= |d|, a
+// close approximation otherwise). Increments of a slowly converging pixel are often smaller
+// than half an ulp of p; rounded into p alone they vanish, always in the same direction, and
+// over the 25 000 dual iterations of a 2048^2 decomposition (K = 50 steps of 500) that alone
+// puts u at 1.5e-4 max|f| and the bands at 1.2e-3 max|f| from the float64 oracle, past the
+// accuracy target. lo is folded into hi (tv_fold) every kFold iterations, so p is stored as
+// one float per component between launches (measured on that workload: u 2.6e-5, bands
+// 1.2e-4 max|f|). w and the epilogue use hi.
+template <bool FAST>
+__device__ __forceinline__ void tv_update_c(float &p1, float &p2, float &l1, float &l2, float G1,
+                                            float G2, float tau) {
+    const float na1 = __fmul_rn(-tau, G1), na2 = __fmul_rn(-tau, G2);
+    const float n2 = __fadd_rn(__fmul_rn(na1, na1), __fmul_rn(na2, na2));
+    const float x = FAST ? sqrt_approx(n2) : __fsqrt_rn(n2);
+    const float nden = __fsub_rn(-1.0f, x);
+    const float ns = FAST ? rcp_approx(nden) : __frcp_rn(nden);
+    const float d1 = __fmaf_rn(__fmaf_rn(p1, x, na1), ns, l1);
+    const float d2 = __fmaf_rn(__fmaf_rn(p2, x, na2), ns, l2);
+    const float h1 = __fadd_rn(p1, d1), h2 = __fadd_rn(p2, d2);
+    l1 = __fsub_rn(d1, __fsub_rn(h1, p1));
+    l2 = __fsub_rn(d2, __fsub_rn(h2, p2));
+    p1 = h1;
+    p2 = h2;
 }
 
 // ---- the same arithmetic on two pixels at once (Blackwell packed f32x2 instructions) ----
@@ -85,17 +119,50 @@ __device__ __forceinline__ float2 sq_norm2(float2 G1, float2 G2) {
 template <bool FAST>
 __device__ __forceinline__ void tv_update2(float2 &p1, float2 &p2, float2 G1, float2 G2,
                                            float tau) {
-    const float2 n2 = sq_norm2(G1, G2);
-    float2 nrm;
-    nrm.x = FAST ? sqrt_approx(n2.x) : __fsqrt_rn(n2.x);
-    nrm.y = FAST ? sqrt_approx(n2.y) : __fsqrt_rn(n2.y);
-    const float2 t2 = make_float2(tau, tau);
-    const float2 den = __ffma2_rn(t2, nrm, make_float2(1.0f, 1.0f));
-    float2 s;
-    s.x = FAST ? rcp_fast(den.x) : __frcp_rn(den.x);
-    s.y = FAST ? rcp_fast(den.y) : __frcp_rn(den.y);
-    p1 = __fmul2_rn(__ffma2_rn(t2, G1, p1), s);
-    p2 = __fmul2_rn(__ffma2_rn(t2, G2, p2), s);
+    const float2 nt2 = make_float2(-tau, -tau);
+    const float2 na1 = __fmul2_rn(nt2, G1), na2 = __fmul2_rn(nt2, G2);
+    const float2 n2 = sq_norm2(na1, na2);
+    float2 x;
+    x.x = FAST ? sqrt_approx(n2.x) : __fsqrt_rn(n2.x);
+    x.y = FAST ? sqrt_approx(n2.y) : __fsqrt_rn(n2.y);
+    const float2 nden = sub2(make_float2(-1.0f, -1.0f), x);
+    float2 ns;
+    ns.x = FAST ? rcp_approx(nden.x) : __frcp_rn(nden.x);
+    ns.y = FAST ? rcp_approx(nden.y) : __frcp_rn(nden.y);
+    p1 = __ffma2_rn(__ffma2_rn(p1, x, na1), ns, p1);
+    p2 = __ffma2_rn(__ffma2_rn(p2, x, na2), ns, p2);
+}
+
+// The fold points of the compensated update: the remainder goes into p with one rounding.
+__device__ __forceinline__ void tv_fold(float &p, float &l) {
+    p = __fadd_rn(p, l);
+    l = 0.0f;
+}
+__device__ __forceinline__ void tv_fold2(float2 &p, float2 &l) {
+    p = __fadd2_rn(p, l);
+    l = make_float2(0.0f, 0.0f);
+}
+
+template <bool FAST>
+__device__ __forceinline__ void tv_update2_c(float2 &p1, float2 &p2, float2 &l1, float2 &l2,
+                                             float2 G1, float2 G2, float tau) {
+    const float2 nt2 = make_float2(-tau, -tau);
+    const float2 na1 = __fmul2_rn(nt2, G1), na2 = __fmul2_rn(nt2, G2);
+    const float2 n2 = sq_norm2(na1, na2);
+    float2 x;
+    x.x = FAST ? sqrt_approx(n2.x) : __fsqrt_rn(n2.x);
+    x.y = FAST ? sqrt_approx(n2.y) : __fsqrt_rn(n2.y);
+    const float2 nden = sub2(make_float2(-1.0f, -1.0f), x);
+    float2 ns;
+    ns.x = FAST ? rcp_approx(nden.x) : __frcp_rn(nden.x);
+    ns.y = FAST ? rcp_approx(nden.y) : __frcp_rn(nden.y);
+    const float2 d1 = __ffma2_rn(__ffma2_rn(p1, x, na1), ns, l1);
+    const float2 d2 = __ffma2_rn(__ffma2_rn(p2, x, na2), ns, l2);
+    const float2 h1 = __fadd2_rn(p1, d1), h2 = __fadd2_rn(p2, d2);
+    l1 = sub2(d1, sub2(h1, p1));
+    l2 = sub2(d2, sub2(h2, p2));
+    p1 = h1;
+    p2 = h2;
 }
 
 }  // namespace tvspec

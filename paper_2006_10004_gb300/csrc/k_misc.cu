@@ -12,11 +12,15 @@ namespace tvspec {
 // Reference dual-iteration kernel: one Chambolle iteration per launch, one thread per pixel,
 // neighbours read from global memory, p_in -> p_out (Chambolle 2004 as used in Sec. 4.3).
 // ---------------------------------------------------------------------------------------------
+// Float32 storage: p is updated in the compensated form as hi + lo, with lo carried between
+// launches in q1 / q2 (in -> out) and folded into hi at the fold points (kFold), exactly as the
+// tiled kernels do in registers; `it` is the iteration's index within the step of n_total.
 template <typename P, bool FAST>
 __global__ void __launch_bounds__(256)
     k_naive(const P *__restrict__ p1i, const P *__restrict__ p2i, P *__restrict__ p1o,
-            P *__restrict__ p2o, const float *__restrict__ gl, int H, int W, int pitch,
-            float tau) {
+            P *__restrict__ p2o, const float *__restrict__ q1i, const float *__restrict__ q2i,
+            float *__restrict__ q1o, float *__restrict__ q2o, const float *__restrict__ gl, int H,
+            int W, int pitch, float tau, int it, int n_total) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= H || j >= W) return;
@@ -31,34 +35,50 @@ __global__ void __launch_bounds__(256)
     const float G1 = (i < H - 1) ? __fsub_rn(w_at(i + 1, j), w) : 0.0f;
     const float G2 = (j < W - 1) ? __fsub_rn(w_at(i, j + 1), w) : 0.0f;
     float a = P1(i, j), b = P2(i, j);
-    tv_update<FAST>(a, b, G1, G2, tau);
-    p1o[(size_t)i * pitch + j] = PStore<P>::store(a);
-    p2o[(size_t)i * pitch + j] = PStore<P>::store(b);
+    const size_t o = (size_t)i * pitch + j;
+    if constexpr (sizeof(P) == 4) {
+        float la = it % kFold != 0 ? q1i[o] : 0.0f, lb = it % kFold != 0 ? q2i[o] : 0.0f;
+        tv_update_c<FAST>(a, b, la, lb, G1, G2, tau);
+        if ((it + 1) % kFold == 0 || it + 1 == n_total) {
+            tv_fold(a, la);
+            tv_fold(b, lb);
+        }
+        q1o[o] = la;
+        q2o[o] = lb;
+    } else {
+        tv_update<FAST>(a, b, G1, G2, tau);
+    }
+    p1o[o] = PStore<P>::store(a);
+    p2o[o] = PStore<P>::store(b);
 }
 
 template <typename P>
 static cudaError_t naive_typed(bool fast, const void *p1i, const void *p2i, void *p1o,
-                               void *p2o, const float *gl, int H, int W, int pitch, float tau,
-                               cudaStream_t st) {
+                               void *p2o, const float *q1i, const float *q2i, float *q1o,
+                               float *q2o, const float *gl, int H, int W, int pitch, float tau,
+                               int it, int n_total, cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((W + 31) / 32, (H + 7) / 8);
     if (fast)
         k_naive<P, true><<<grid, block, 0, st>>>((const P *)p1i, (const P *)p2i, (P *)p1o,
-                                                 (P *)p2o, gl, H, W, pitch, tau);
+                                                 (P *)p2o, q1i, q2i, q1o, q2o, gl, H, W, pitch, tau, it, n_total);
     else
         k_naive<P, false><<<grid, block, 0, st>>>((const P *)p1i, (const P *)p2i, (P *)p1o,
-                                                  (P *)p2o, gl, H, W, pitch, tau);
+                                                  (P *)p2o, q1i, q2i, q1o, q2o, gl, H, W, pitch, tau, it, n_total);
     return cudaGetLastError();
 }
 
 cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,
-                         void *p1_out, void *p2_out, const float *gl, int H, int W, int pitch,
-                         float tau, cudaStream_t st) {
+                         void *p1_out, void *p2_out, const float *q1_in, const float *q2_in,
+                         float *q1_out, float *q2_out, const float *gl, int H, int W, int pitch,
+                         float tau, int it, int n_total, cudaStream_t st) {
     switch (p_storage) {
-        case 0: return naive_typed<float>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
-        case 1: return naive_typed<__half>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
-        case 2: return naive_typed<__nv_bfloat16>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
-        case 3: return naive_typed<short>(fast, p1_in, p2_in, p1_out, p2_out, gl, H, W, pitch, tau, st);
+        case 0:
+            if (!q1_in || !q2_in || !q1_out || !q2_out) return cudaErrorInvalidValue;
+            return naive_typed<float>(fast, p1_in, p2_in, p1_out, p2_out, q1_in, q2_in, q1_out, q2_out, gl, H, W, pitch, tau, it, n_total, st);
+        case 1: return naive_typed<__half>(fast, p1_in, p2_in, p1_out, p2_out, nullptr, nullptr, nullptr, nullptr, gl, H, W, pitch, tau, it, n_total, st);
+        case 2: return naive_typed<__nv_bfloat16>(fast, p1_in, p2_in, p1_out, p2_out, nullptr, nullptr, nullptr, nullptr, gl, H, W, pitch, tau, it, n_total, st);
+        case 3: return naive_typed<short>(fast, p1_in, p2_in, p1_out, p2_out, nullptr, nullptr, nullptr, nullptr, gl, H, W, pitch, tau, it, n_total, st);
         default: return cudaErrorInvalidValue;
     }
 }

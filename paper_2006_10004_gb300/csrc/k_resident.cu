@@ -119,11 +119,13 @@ __global__ void __launch_bounds__(32 * RW, MINB)
 
     // u_0 = f (Eq. TVflow), g/dt of step 0, p = 0
     float2 p1[R][VP], p2[R][VP], gl[R][VP];
+    float2 l1[R][VP], l2[R][VP];  // low parts of p (zero between steps: a step ends at a fold point)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
 #pragma unroll
         for (int j = 0; j < VP; ++j) {
             p1[r][j] = p2[r][j] = gl[r][j] = make_float2(0.0f, 0.0f);
+            l1[r][j] = l2[r][j] = make_float2(0.0f, 0.0f);
             float g2[2] = {0.0f, 0.0f};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -145,7 +147,8 @@ __global__ void __launch_bounds__(32 * RW, MINB)
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int j = 0; j < VP; ++j) p1[r][j] = p2[r][j] = make_float2(0.0f, 0.0f);
+                for (int j = 0; j < VP; ++j)
+                    p1[r][j] = p2[r][j] = l1[r][j] = l2[r][j] = make_float2(0.0f, 0.0f);
         }
         if (RW > 1) {
             FPack<V> q;
@@ -158,10 +161,12 @@ __global__ void __launch_bounds__(32 * RW, MINB)
         }
         __syncthreads();
         if (exact)  // the image fills the tile: masks only on its last row and column
-            tiled_iterate<V, R, RW, FAST, kEdgeExact, true>(p1, p2, gl, d.n_inner, tau, 0u, 0u,
+            tiled_iterate<V, R, RW, FAST, kEdgeExact, true, true>(p1, p2, l1, l2, gl, d.n_inner, 0,
+                                                                  d.n_inner, tau, 0u, 0u,
                                                             s_p1b, s_wt, lane, wy);
         else
-            tiled_iterate<V, R, RW, FAST, kEdgeMasked, true>(p1, p2, gl, d.n_inner, tau, m1, m2,
+            tiled_iterate<V, R, RW, FAST, kEdgeMasked, true, true>(p1, p2, l1, l2, gl, d.n_inner, 0,
+                                                                   d.n_inner, tau, m1, m2,
                                                              s_p1b, s_wt, lane, wy);
         // p to global for the divergence's neighbours
 #pragma unroll
@@ -241,7 +246,11 @@ static const ResidentVariant kResident[] = {
 };
 #undef TVSPEC_RESIDENT
 static constexpr int kNumResident = (int)(sizeof(kResident) / sizeof(kResident[0]));
-static const int kAutoOrder[] = {6, 1, 2};
+// The compensated update keeps two more floats per pixel in registers: the 16-pixel layouts
+// budgeted for 3 or 4 CTAs per SM spill heavily (measured on 3000 crops of 64^2, K = 50, 300
+// iterations: 3.7 k / 2.8 k crops/s), the 512-thread 8-pixel layout does not (13.5 k crops/s,
+// as the 2-CTA 16-pixel layout).
+static const int kAutoOrder[] = {4, 1, 2};
 
 static bool resident_holds(int i, int H, int W) {
     return W <= 32 * kResident[i].V && H <= kResident[i].RW * kResident[i].R;

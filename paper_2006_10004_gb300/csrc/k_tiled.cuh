@@ -57,10 +57,15 @@ constexpr int kEdgeNone = 0, kEdgeMasked = 1, kEdgeExact = 2;
 // horizontal pairs (columns 2q, 2q+1 of the lane) with packed f32x2 arithmetic.
 // ZERO_LEFT: the tile's first column is the image's first column (no halo), so lane 0's left
 // neighbour p2_{i,-1} is 0 rather than a halo value.
-template <int V, int R, int RW, bool FAST, int EDGE, bool ZERO_LEFT = false>
+// COMP (float32 storage): p is held as hi + lo (p1 + l1, p2 + l2), updated by tv_update2_c and
+// folded at the fold points (kFold); the launch covers iterations [it0, it0 + n_iter) of a step
+// of n_total, with it0 a fold point, so l1 / l2 start and end at zero. Otherwise l1 / l2 are not
+// touched.
+template <int V, int R, int RW, bool FAST, int EDGE, bool ZERO_LEFT = false, bool COMP = false>
 __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
-                                              const float2 (&gl)[R][V / 2], int n_iter,
-                                              float tau, unsigned m1bits, unsigned m2bits,
+                                              float2 (&l1)[R][V / 2], float2 (&l2)[R][V / 2],
+                                              const float2 (&gl)[R][V / 2], int n_iter, int it0,
+                                              int n_total, float tau, unsigned m1bits, unsigned m2bits,
                                               float (*s_p1b)[32 * V], float (*s_wt)[32 * V],
                                               int lane, int wy) {
     constexpr unsigned FULL = 0xffffffffu;
@@ -130,7 +135,22 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
                     if (r == R - 1 && wy == RW - 1) G1 = make_float2(0.0f, 0.0f);  // last row
                     if (j == VP - 1 && lane == 31) G2.y = 0.0f;                    // last column
                 }
-                tv_update2<FAST>(p1[r][j], p2[r][j], G1, G2, tau);
+                if constexpr (COMP)
+                    tv_update2_c<FAST>(p1[r][j], p2[r][j], l1[r][j], l2[r][j], G1, G2, tau);
+                else
+                    tv_update2<FAST>(p1[r][j], p2[r][j], G1, G2, tau);
+            }
+        }
+        if constexpr (COMP) {
+            const int done = it0 + it + 1;  // iterations of the step completed
+            if (done % kFold == 0 || done == n_total) {  // uniform over the CTA
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int j = 0; j < VP; ++j) {
+                        tv_fold2(p1[r][j], l1[r][j]);
+                        tv_fold2(p2[r][j], l2[r][j]);
+                    }
             }
         }
         if (RW > 1) {
@@ -213,7 +233,9 @@ __device__ __forceinline__ bool tma_tile_load(const TmaMaps &tm, int xs, int ys,
 }
 
 // One CTA's work on tile (tx, ty) of image d: load, iterate, store the centre. TMA: the tile
-// is loaded by tma_tile_load from the maps tm (float32 p only).
+// is loaded by tma_tile_load from the maps tm (float32 p only). Float32 storage updates p with
+// the compensated form (hi + lo in registers, folded every kFold iterations); 16-bit storage
+// rounds p between launches anyway and updates it directly.
 template <int V, int R, int RW, int TB, typename P, bool FAST, bool TMA = false>
 __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int gstep, int blk,
                                            int depth, float tau, const TmaMaps *tm = nullptr) {
@@ -250,7 +272,15 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
     const int ry = ys + wy * R;
     const bool col_ok = (cx >= 0) && (cx < pitch);
 
+    constexpr bool COMP = sizeof(P) == 4;
     float2 p1[R][VP], p2[R][VP], gl[R][VP];
+    float2 l1[R][VP], l2[R][VP];  // low parts of p: zero at a launch's start (a fold point)
+    if constexpr (COMP) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < VP; ++j) l1[r][j] = l2[r][j] = make_float2(0.0f, 0.0f);
+    }
     if constexpr (TMA) {
         static_assert(sizeof(P) == 4, "TMA tile loads read float32 p");
         if (!tma_tile_load<V, R, RW>(*tm, xs, ys, d.status, p1, p2, gl, lane, wy)) return;
@@ -288,8 +318,9 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
 
     const bool interior = ys >= 0 && ys + TH <= H - 1 && xs >= 0 && xs + TW <= W - 1;
     if (interior) {
-        tiled_iterate<V, R, RW, FAST, kEdgeNone>(p1, p2, gl, n_iter, tau, 0u, 0u, s_p1b, s_wt, lane,
-                                             wy);
+        tiled_iterate<V, R, RW, FAST, kEdgeNone, false, COMP>(p1, p2, l1, l2, gl, n_iter, blk * depth,
+                                                              d.n_inner, tau, 0u, 0u, s_p1b, s_wt,
+                                                              lane, wy);
     } else {
         unsigned m1 = 0u, m2 = 0u;
 #pragma unroll
@@ -303,8 +334,9 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
                 if (y >= 0 && y < H && c >= 0 && c < W - 1) m2 |= 1u << (r * V + v);
             }
         }
-        tiled_iterate<V, R, RW, FAST, kEdgeMasked>(p1, p2, gl, n_iter, tau, m1, m2, s_p1b, s_wt, lane,
-                                            wy);
+        tiled_iterate<V, R, RW, FAST, kEdgeMasked, false, COMP>(p1, p2, l1, l2, gl, n_iter, blk * depth,
+                                                                d.n_inner, tau, m1, m2, s_p1b, s_wt,
+                                                                lane, wy);
     }
 
     // store the exact centre into the other copy (the halo this CTA read belongs to other
@@ -380,7 +412,7 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     X(8, 2, 8, 4, 4, 0) \
     X(9, 4, 4, 16, 12, 0) \
     X(10, 2, 8, 16, 12, 0) \
-    X(11, 2, 4, 8, 2, 0) \
+    X(11, 2, 4, 8, 4, 0) \
     X(12, 2, 4, 16, 8, 0) \
     X(13, 2, 4, 32, 8, 0) \
     X(14, 2, 2, 32, 8, 0) \

@@ -103,7 +103,7 @@ tvspec_status make_job(const tvspec_request &req, Job *out) {
 // The part from p1 to the status word is cleared at the start of every decomposition.
 // ---------------------------------------------------------------------------------------------
 struct SlotLayout {
-    size_t band, fH, fres, f, p1, p2, q1, q2, gl, acc, facc, filt, bands, partials, ctr, ua, ub,
+    size_t band, fH, fres, f, p1, p2, q1, q2, l1a, l2a, l1b, l2b, gl, acc, facc, filt, bands, partials, ctr, flags, ua, ub,
         u3, res, S, tr, spar, ppar, zero_begin, zero_end, total;
     std::vector<std::pair<size_t, size_t>> guards;  // (offset, bytes) between and around arrays
 };
@@ -111,8 +111,7 @@ struct SlotLayout {
 // guard > 0 (test_guard_bytes, a multiple of 256): a guard region before the first array and
 // after every array (its alignment slack plus `guard` bytes), for the write checks of
 // slot_check_guards.
-static SlotLayout layout_for(int H, int W, int K, int nb, int storage,
-                             [[maybe_unused]] bool naive, bool trace, int nf = 0,
+static SlotLayout layout_for(int H, int W, int K, int nb, int storage, bool naive, bool trace, int nf = 0,
                              bool par = false, size_t guard = 0) {
     SlotLayout L{};
     const size_t N = (size_t)H * W;
@@ -136,11 +135,19 @@ static SlotLayout layout_for(int H, int W, int K, int nb, int storage,
     L.p2 = take(pb);
     L.q1 = take(pb);
     L.q2 = take(pb);
+    // float32 storage with the one-iteration reference kernel: the low parts of p (p = hi + lo)
+    // of both copies, carried between its launches (the tiled kernels keep them in registers)
+    const size_t lb = (storage == 0 && naive) ? (size_t)H * pitch * 4 : 0;
+    L.l1a = take(lb);
+    L.l2a = take(lb);
+    L.l1b = take(lb);
+    L.l2b = take(lb);
     L.gl = take((size_t)H * pitch * 4);
     L.acc = take(N * 8);
     L.bands = take((size_t)nb * N * 4);
     L.partials = take((size_t)ep_blocks_for(H, W) * 8);
     L.ctr = take(16);
+    L.flags = take((size_t)max_tiles_for(H, W) * 4);  // persistent kernel's tile epochs
     L.zero_end = off;
     L.facc = take((size_t)nf * N * 8);  // written at k = 1 before any read
     L.filt = take((size_t)nf * N * 4);
@@ -201,12 +208,19 @@ tvspec_status slot_alloc(Slot *s, const Job &j, int storage, bool naive, cudaStr
     x.p2[0] = base + L.p2;
     x.p1[1] = base + L.q1;
     x.p2[1] = base + L.q2;
+    if (storage == 0 && naive) {
+        x.lo1[0] = (float *)(base + L.l1a);
+        x.lo2[0] = (float *)(base + L.l2a);
+        x.lo1[1] = (float *)(base + L.l1b);
+        x.lo2[1] = (float *)(base + L.l2b);
+    }
     x.gl = (float *)(base + L.gl);
     x.acc = (double *)(base + L.acc);
     x.bands = (float *)(base + L.bands);
     x.partials = (double *)(base + L.partials);
     x.counter = (unsigned *)(base + L.ctr);
     x.status = x.counter + 1;
+    x.tile_flags = (unsigned *)(base + L.flags);
     x.ua = (double *)(base + L.ua);
     x.ub = (double *)(base + L.ub);
     x.u3 = (double *)(base + L.u3);
@@ -287,6 +301,10 @@ ImgDesc slot_desc(const Slot &s, int s0) {
     d.p1[1] = s.p1[1];
     d.p2[0] = s.p2[0];
     d.p2[1] = s.p2[1];
+    for (int c = 0; c < 2; ++c) {
+        d.q1[c] = s.lo1[c];
+        d.q2[c] = s.lo2[c];
+    }
     d.gl = s.gl;
     d.ua = s.ua;
     d.ub = s.ub;
@@ -299,6 +317,7 @@ ImgDesc slot_desc(const Slot &s, int s0) {
     d.partials = s.partials;
     d.counter = s.counter;
     d.status = s.status;
+    d.tile_flags = s.tile_flags;
     d.band_of_k = s.band_of_k;
     d.n_filters = s.n_filters;
     d.filt_H = s.filt_H;
@@ -407,11 +426,14 @@ tvspec_status launchset_build(LaunchSet *ls, const std::vector<ImgDesc> &descs, 
 // not depend on the tiling), so the autotuner may pick freely; with 16-bit storage of p the
 // rounding points depend on the iterations per launch, so there the depth is fixed.
 // ---------------------------------------------------------------------------------------------
+// With float32 storage the iterations per launch are a multiple of kFold (every launch starts
+// and ends at a fold point of the compensated update): a shape's most, or the configured
+// temporal block, rounded down to one (at least kFold; every shape allows kFold).
 static int default_depth(const tvspec_config &c, int shape) {
     const int TB = tiled_shape(shape).TB;
-    if (c.temporal_block > 0) return std::min(c.temporal_block, TB);
-    if (c.p_storage != TVSPEC_P_FP32) return std::min(8, TB);
-    return TB;
+    if (c.p_storage != TVSPEC_P_FP32) return c.temporal_block > 0 ? std::min(c.temporal_block, TB) : std::min(8, TB);
+    const int want = c.temporal_block > 0 ? std::min(c.temporal_block, TB) : TB;
+    return std::max(kFold, want / kFold * kFold);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -455,7 +477,8 @@ static void tune_cache_load(tvspec_plan *plan) {
         if (!(in >> prefix >> key >> shape >> depth)) continue;
         if (!(in >> pdl)) pdl = 0;
         if (prefix != plan->tune_prefix) continue;
-        if (shape < 0 || shape >= tiled_shape_count() || depth < 1 || depth > tiled_shape(shape).TB)
+        if (shape < 0 || shape >= tiled_shape_count() || depth < 1 || depth > tiled_shape(shape).TB ||
+            (plan->cfg.p_storage == TVSPEC_P_FP32 && depth % kFold != 0))
             continue;
         plan->tune[key] = {shape, depth, pdl != 0};
     }
@@ -652,8 +675,9 @@ static tvspec_status enqueue_iterations(tvspec_plan *plan, LaunchSet &ls,
         for (int it = 0; it < n_it; ++it) {
             const int src = p_copy(k, n_it, it);
             cudaError_t e = launch_naive(c.p_storage, c.fast_math != 0, d.p1[src], d.p2[src],
-                                         d.p1[src ^ 1], d.p2[src ^ 1], s.gl, s.H, s.W, s.pitch,
-                                         c.tau, st);
+                                         d.p1[src ^ 1], d.p2[src ^ 1], d.q1[src], d.q2[src],
+                                         d.q1[src ^ 1], d.q2[src ^ 1], s.gl, s.H, s.W, s.pitch,
+                                         c.tau, it, n_it, st);
             if (e != cudaSuccess) return fail_cuda(e, "reference kernel launch");
             ++*nk;
         }
@@ -669,7 +693,18 @@ static tvspec_status enqueue_iterations(tvspec_plan *plan, LaunchSet &ls,
     const int nt = ls.tile_prefix[n_active];
     // one image: its descriptor goes by value, no table reads before the tile loads
     const bool one = ls.n == 1 && n_active == 1 && tiled_one_available(c.p_storage);
-    if (one && c.persistent && ls.h_descs[0].counter != nullptr && nblk > 1 &&
+    if (one && c.persistent == 2 && ls.h_descs[0].tile_flags != nullptr && nblk > 1 &&
+        step_nbr_fits(ls.shape, c.fast_math != 0, nt)) {
+        // the whole step in one cooperative launch, each tile waiting only on its neighbours
+        cudaError_t e = launch_step_nbr(ls.shape, c.fast_math != 0, ls.h_descs[0], gstep,
+                                        ls.depth, c.tau,
+                                        (unsigned long long)c.barrier_timeout_ms * 1000000ull,
+                                        c.test_barrier_noshow, st);
+        if (e != cudaSuccess) return fail_cuda(e, "persistent kernel launch");
+        ++*nk;
+        return TVSPEC_OK;
+    }
+    if (one && c.persistent == 1 && ls.h_descs[0].counter != nullptr && nblk > 1 &&
         step_coop_fits(ls.shape, c.fast_math != 0, nt)) {
         // the whole step in one cooperative launch (tiles resident, bounded-wait barriers)
         cudaError_t e = launch_step_coop(ls.shape, c.fast_math != 0, ls.h_descs[0], gstep,
@@ -703,6 +738,10 @@ tvspec_status enqueue_step(tvspec_plan *plan, LaunchSet &ls, std::vector<Slot *>
             for (int cpy = 0; cpy < 2; ++cpy) {
                 TV_CK(cudaMemsetAsync(slots[i]->p1[cpy], 0, slots[i]->p_bytes, st));
                 TV_CK(cudaMemsetAsync(slots[i]->p2[cpy], 0, slots[i]->p_bytes, st));
+                if (slots[i]->lo1[cpy]) {
+                    TV_CK(cudaMemsetAsync(slots[i]->lo1[cpy], 0, slots[i]->p_bytes, st));
+                    TV_CK(cudaMemsetAsync(slots[i]->lo2[cpy], 0, slots[i]->p_bytes, st));
+                }
             }
         }
     }
@@ -734,6 +773,10 @@ static tvspec_status enqueue_step_split(tvspec_plan *plan, LaunchSet &ls, std::v
             for (int cpy = 0; cpy < 2; ++cpy) {
                 TV_CK(cudaMemsetAsync(slots[i]->p1[cpy], 0, slots[i]->p_bytes, st));
                 TV_CK(cudaMemsetAsync(slots[i]->p2[cpy], 0, slots[i]->p_bytes, st));
+                if (slots[i]->lo1[cpy]) {
+                    TV_CK(cudaMemsetAsync(slots[i]->lo1[cpy], 0, slots[i]->p_bytes, st));
+                    TV_CK(cudaMemsetAsync(slots[i]->lo2[cpy], 0, slots[i]->p_bytes, st));
+                }
             }
         }
     }
@@ -1287,6 +1330,7 @@ tvspec_status tvspec_plan_create(const tvspec_config *cfg, int device, tvspec_pl
     if (c.max_batch < 0) return fail(TVSPEC_EINVAL, "max_batch must be >= 0");
     if (c.barrier_timeout_ms < 1) return fail(TVSPEC_EINVAL, "barrier_timeout_ms must be >= 1");
     if (c.resident < 0 || c.resident > 2) return fail(TVSPEC_EINVAL, "resident must be 0, 1 or 2");
+    if (c.persistent < 0 || c.persistent > 2) return fail(TVSPEC_EINVAL, "persistent must be 0, 1 or 2");
     if (c.acc_mode < 0 || c.acc_mode > 1) return fail(TVSPEC_EINVAL, "acc_mode must be 0 or 1");
     if (c.resident_variant < -1 || c.resident_variant >= resident_variant_count())
         return fail(TVSPEC_EINVAL, "resident_variant out of range");
@@ -1497,6 +1541,10 @@ tvspec_status tvspec_decompose_steps(tvspec_plan *plan, const tvspec_request *re
         if (was != now) {
             TV_CK(cudaMemcpyAsync(sl.p1[now], sl.p1[was], sl.p_bytes, cudaMemcpyDeviceToDevice, st));
             TV_CK(cudaMemcpyAsync(sl.p2[now], sl.p2[was], sl.p_bytes, cudaMemcpyDeviceToDevice, st));
+            if (sl.lo1[now]) {
+                TV_CK(cudaMemcpyAsync(sl.lo1[now], sl.lo1[was], sl.p_bytes, cudaMemcpyDeviceToDevice, st));
+                TV_CK(cudaMemcpyAsync(sl.lo2[now], sl.lo2[was], sl.p_bytes, cudaMemcpyDeviceToDevice, st));
+            }
         }
     }
     bool pending = false;
@@ -1614,7 +1662,11 @@ tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float
     cudaStream_t st = stream ? (cudaStream_t)stream : plan->stream;
     // copy 1 of the dual field: a plan-owned buffer of the caller's pitched size
     const size_t pb = (size_t)H * pitch * 4;
-    const size_t need = 2 * pb + 256;  // + counter, status and barrier words
+    const size_t flag_bytes = ((size_t)max_tiles_for(H, W) * 4 + 255) / 256 * 256;
+    // + counter, status, barrier and tile words, + the low parts of p of both copies (zero at
+    // the start of every call: the caller's p is taken as exact)
+    const size_t lb = (pb + 255) / 256 * 256;
+    const size_t need = 2 * pb + 256 + flag_bytes + 4 * lb;
     if (plan->ping_bytes < need) {
         TV_CK(cudaStreamSynchronize(st));
         cudaFree(plan->ping);
@@ -1624,7 +1676,8 @@ tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float
         plan->ping_bytes = need;
     }
     unsigned *words = reinterpret_cast<unsigned *>((char *)plan->ping + 2 * pb);
-    TV_CK(cudaMemsetAsync(words, 0, 16, st));
+    char *lo = (char *)plan->ping + 2 * pb + 256 + flag_bytes;
+    TV_CK(cudaMemsetAsync(words, 0, 256 + flag_bytes + 4 * lb, st));
     ImgDesc d{};
     d.p1[0] = p1;
     d.p2[0] = p2;
@@ -1632,6 +1685,11 @@ tvspec_status tvspec_chambolle_iterate(tvspec_plan *plan, const float *gl, float
     d.p2[1] = (char *)plan->ping + pb;
     d.counter = words;
     d.status = words + 1;
+    d.tile_flags = words + 64;
+    for (int c = 0; c < 2; ++c) {
+        d.q1[c] = reinterpret_cast<float *>(lo + (2 * c) * lb);
+        d.q2[c] = reinterpret_cast<float *>(lo + (2 * c + 1) * lb);
+    }
     d.gl = const_cast<float *>(gl);
     d.H = H;
     d.W = W;

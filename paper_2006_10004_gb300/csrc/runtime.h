@@ -59,11 +59,13 @@ struct Slot {
     size_t zero_off = 0, zero_bytes = 0;  // region cleared at the start of every decomposition
     float *f = nullptr;
     void *p1[2] = {nullptr, nullptr}, *p2[2] = {nullptr, nullptr};  // two copies of p
+    float *lo1[2] = {nullptr, nullptr}, *lo2[2] = {nullptr, nullptr};  // their low parts (fp32)
     float *gl = nullptr;
     double *ua = nullptr, *ub = nullptr, *u3 = nullptr, *acc = nullptr;
     float *bands = nullptr, *residual = nullptr;
     double *S = nullptr, *utrace = nullptr, *partials = nullptr;
     unsigned *counter = nullptr, *status = nullptr;
+    unsigned *tile_flags = nullptr;  // epochs of the neighbour-synchronised persistent kernel
     signed char *band_of_k = nullptr;
     int n_filters = 0;
     double *filt_H = nullptr, *filt_res = nullptr, *facc = nullptr;

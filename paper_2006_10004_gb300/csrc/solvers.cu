@@ -403,6 +403,12 @@ static tvspec_status rof_solve_locked(tvspec_plan *plan, tvspec_rof_request &q, 
             d.p1[1] = B.p1[cur_p ^ 1];
             d.p2[0] = B.p2[cur_p];
             d.p2[1] = B.p2[cur_p ^ 1];
+            // the low parts of p (p = hi + lo) in FGP's momentum buffers, which Chambolle's
+            // iteration does not use (zero from the workspace clear, carried across checks)
+            d.q1[0] = B.r1[cur_p];
+            d.q1[1] = B.r1[cur_p ^ 1];
+            d.q2[0] = B.r2[cur_p];
+            d.q2[1] = B.r2[cur_p ^ 1];
             d.gl = B.gl;
             d.counter = B.words + 4;
             d.status = B.words + 5;

@@ -8,6 +8,14 @@
 
 namespace tvspec {
 
+// Float32 storage of p: each pixel's dual value is held in registers as hi + lo (Fast2Sum
+// compensation of the update, chambolle_math.cuh), and lo is folded into hi after every
+// iteration i (0-based within an ROF step) with (i + 1) % kFold == 0 and after the step's last
+// iteration. Every launch therefore starts and ends at a fold point (iterations per launch are
+// multiples of kFold), p is stored as one float32 per component, and the results do not depend
+// on the tile shape or the iterations per launch.
+constexpr int kFold = 4;
+
 // Most band edges a request may carry (n_edges <= kMaxEdges).
 constexpr int kMaxEdges = 65;
 // Pixels of one row chunk handled by one epilogue block.
@@ -25,6 +33,10 @@ struct ImgDesc {
     // launch of dual iterations reads one copy and writes the other (tiles read halo pixels
     // that neighbouring tiles of the same launch update)
     void *p1[2], *p2[2];
+    // float32 storage, reference kernel only (one iteration per launch, so a launch may end
+    // between fold points): the low parts of p, same layout and copies as p1 / p2; nullptr
+    // elsewhere (the tiled kernels keep them in registers)
+    float *q1[2], *q2[2];
     float *gl;              // g / lambda of the current ROF step, float32, pitched
     double *ua, *ub;        // u ping-pong (compact H*W): u_k is ua for even k, ub for odd k
     double *u3;             // third u buffer of the split epilogue: u_k in {ua, ub, u3}[k % 3]
@@ -37,6 +49,8 @@ struct ImgDesc {
     unsigned *counter;      // epilogue blocks finished in the current step; counter[2..3]
                             // hold the persistent kernel's grid barrier (arrivals, generation)
     unsigned *status;       // device status bits (counter + 1)
+    unsigned *tile_flags;   // one epoch word per tile of the neighbour-synchronised persistent
+                            // kernel (zero at the start of a decomposition), or nullptr
     const signed char *band_of_k;  // K entries: band of t_k (host-decided in float64), -1 none
     int n_filters;          // spectral filters fused into the epilogue
     const double *filt_H;   // n_filters x (K-1): H_q(t_k) at q*(K-1) + k-1
@@ -142,6 +156,14 @@ bool step_coop_fits(int shape, bool fast, int n_tiles);
 cudaError_t launch_step_coop(int shape, bool fast, const ImgDesc &d, int gstep, int depth,
                              float tau, unsigned long long timeout_ns, int noshow_block,
                              cudaStream_t st);
+// The same persistent step with neighbour-only synchronisation (epoch flags in d.tile_flags,
+// one word per tile of the shape); step_nbr_fits says whether all tiles can be resident.
+bool step_nbr_fits(int shape, bool fast, int n_tiles);
+cudaError_t launch_step_nbr(int shape, bool fast, const ImgDesc &d, int gstep, int depth,
+                            float tau, unsigned long long timeout_ns, int noshow_block,
+                            cudaStream_t st);
+// Most tiles any tile shape makes of an H x W image (the size of a tile-flag array).
+int max_tiles_for(int H, int W);
 
 // Resident small-image kernel: the whole decomposition of each image idx[0..n) of descs in
 // one CTA (fp32). resident_variant_for gives the variant whose tile holds an H x W image, or -1.
@@ -153,9 +175,11 @@ cudaError_t launch_resident(int variant, bool fast, const ImgDesc *descs, const 
                             float tau, int warm_start, bool parseval, cudaStream_t st);
 
 // One iteration per launch over one image (reference GPU kernel): p_in -> p_out.
+// Float32 storage needs the low-part arrays (q*_in of iteration `it` within a step of n_total).
 cudaError_t launch_naive(int p_storage, bool fast, const void *p1_in, const void *p2_in,
-                         void *p1_out, void *p2_out, const float *gl, int H, int W, int pitch,
-                         float tau, cudaStream_t st);
+                         void *p1_out, void *p2_out, const float *q1_in, const float *q2_in,
+                         float *q1_out, float *q2_out, const float *gl, int H, int W, int pitch,
+                         float tau, int it, int n_total, cudaStream_t st);
 
 // Start of a decomposition for every image owning one of the epilogue blocks
 // [block_offset, block_offset + n_blocks) of the ep_img/ep_base list:

@@ -57,8 +57,9 @@ def test_resumed_run_is_bit_identical(tv, H, W):
 
 
 def test_resume_in_another_plan_with_another_launch_parity(tv):
-    # 40 iterations: 5 launches per step at depth 8 (tile 24), 7 at depth 6 (tile 26), 10 at
-    # depth 4 (tile 4): the copy of p a step reads differs, the resumed run must move it
+    # 40 iterations: 5 launches per step at depth 8 (tile 24), 10 at depth 4 (tiles 4 and 26,
+    # whose 6-iteration halo runs 4 per launch, a multiple of the fold interval): the copy of p
+    # a step reads differs, the resumed run must move it
     f = _img(150, 140, 3)
     args = (f, 0.5, 9, 40, syn.DYADIC_EDGES)
     with tv.Plan(0) as p:

@@ -98,7 +98,8 @@ def test_every_tile_shape_and_depth_bit_identical(tv):
     with tv.Plan(0, kernel=tv.KERNEL_NAIVE) as p:
         base = p.decompose(*args, trace=True)
     for i, s in enumerate(tv.tile_shapes()):
-        for depth in sorted({1, 3, s["TB"]}):
+        # iterations per launch: multiples of the compensated update's fold interval (4)
+        for depth in sorted({4, s["TB"] // 4 * 4}):
             with tv.Plan(0, kernel=tv.KERNEL_TILED, tile=i, temporal_block=depth) as p:
                 out = p.decompose(*args, trace=True)
                 assert p.stats()["last_tile"] == i
@@ -187,21 +188,46 @@ def test_resident_batch_of_crops(tv):
         assert_parity(out, oracle.decompose(*job), job[0], "crop")
 
 
-def test_persistent_step_kernel_bit_identical(tv):
-    # one cooperative launch per step (tiles resident, grid barriers) vs one launch per block
-    for H, W in [(256, 300), (512, 512), (37, 53)]:
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_persistent_step_kernel_bit_identical(tv, persistent):
+    # one cooperative launch per step (tiles resident; grid barriers, or waits on the
+    # neighbouring tiles' progress only) vs one launch per block
+    for H, W in [(256, 300), (512, 512), (37, 53), (1, 700), (700, 1)]:
         f = _img(H, W, 11 + H)
         args = (f, 0.5, 4, 41, syn.DYADIC_EDGES)
-        with tv.Plan(0, persistent=1) as a, tv.Plan(0, persistent=0) as b:
-            _same(a.decompose(*args, trace=True), b.decompose(*args, trace=True))
+        with tv.Plan(0, persistent=persistent) as a, tv.Plan(0, persistent=0) as b:
+            got = a.decompose(*args, trace=True)
+            n0 = a.stats()["kernel_launches"]
+            again = a.decompose(*args, trace=True)
+            # one dual-iteration launch per step (+ the two epilogue parts, + the init)
+            assert a.stats()["kernel_launches"] - n0 <= 3 * 4 + 1
+            _same(got, b.decompose(*args, trace=True))
+            _same(again, got)
 
 
-def test_persistent_barrier_timeout_is_reported_and_plan_recovers(tv):
-    # fault injection on the host side of the contract: one CTA never arrives at its barrier,
-    # the others give up after the bounded wait and the call reports TVSPEC_ETIMEOUT; the
-    # device stays usable
+@pytest.mark.parametrize("tile", [5, 11, 14, 20, 24, 26])
+def test_neighbour_synchronised_kernel_every_depth_bit_identical(tv, tile):
+    # the neighbour-flag persistent kernel against the reference kernel for several tile
+    # shapes and depths, on an image with many tiles and ragged edges; the flags must also
+    # carry over from step to step within a decomposition (epochs keep increasing)
+    f = _img(300, 413, 5 + tile)
+    args = (f, 0.5, 5, 29, syn.DYADIC_EDGES)
+    with tv.Plan(0, kernel=tv.KERNEL_NAIVE) as p:
+        base = p.decompose(*args, trace=True)
+    s = tv.tile_shapes()[tile]
+    for depth in sorted({4, s["TB"] // 4 * 4}):
+        with tv.Plan(0, kernel=tv.KERNEL_TILED, tile=tile, temporal_block=depth, persistent=2) as p:
+            _same(p.decompose(*args, trace=True), base)
+            _same(p.decompose(*args, trace=True), base)  # graph replay: flags cleared per run
+
+
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_persistent_barrier_timeout_is_reported_and_plan_recovers(tv, persistent):
+    # fault injection on the host side of the contract: one CTA never arrives at its barrier
+    # (or never publishes its progress), the others give up after the bounded wait and the
+    # call reports TVSPEC_ETIMEOUT; the device stays usable
     f = _img(200, 200, 12)
-    with tv.Plan(0, persistent=1, barrier_timeout_ms=20, test_barrier_noshow=0) as p:
+    with tv.Plan(0, persistent=persistent, barrier_timeout_ms=20, test_barrier_noshow=0) as p:
         with pytest.raises(tv.TvSpecError) as ei:
             p.decompose(f, 0.5, 3, 30, syn.DYADIC_EDGES)
         assert ei.value.status == tv.ETIMEOUT
@@ -462,6 +488,31 @@ def test_serving_results_match_alone(tv):
         for (t, out), job in zip(tickets, jobs):
             alone = p.decompose(*job, trace=True)
             _same(out, alone)
+
+
+def test_serving_admits_a_request_mid_flight_same_as_alone(tv):
+    # Continuous batching, forced by construction rather than by timing: with two slots, A
+    # (short) and B (long) take both; C waits in the queue until A retires, so C joins while B
+    # is on the GPU between two of its steps, and C's steps then run in the same launches as
+    # B's. C must give the bits it gives alone, and match the oracle; B, whose launches changed
+    # when A left and C joined, must too.
+    A = (_img(96, 80, 301), 0.5, 6, 40, syn.DYADIC_EDGES)
+    B = (_img(128, 150, 302), 0.5, 2000, 40, syn.DYADIC_EDGES)
+    C = (_img(70, 111, 303), 0.5, 8, 40, syn.DYADIC_EDGES)
+    with tv.Plan(0, max_batch=2) as p:
+        ta, oa = p.submit(*A, trace=True)
+        tb, ob = p.submit(*B)
+        tc, oc = p.submit(*C, trace=True)
+        assert p.wait(tc, 120000) == tv.OK
+        # C is done while B (2000 steps, admitted no later than A's retirement after 6) still runs
+        b_running = p.poll(tb) == tv.ENOTREADY
+        assert p.wait(ta, 120000) == tv.OK and p.wait(tb, 120000) == tv.OK
+        assert b_running
+        for out, job in ((oa, A), (ob, B), (oc, C)):
+            alone = p.decompose(*job, trace="u" in out)
+            _same(out, alone)
+    ref = oracle.decompose(*C, trace=True)
+    assert_parity(oc, ref, C[0], "served mid-flight")
 
 
 def test_serving_budget_and_cancel(tv):
