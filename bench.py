@@ -43,7 +43,7 @@ def kernel_source_hash() -> str:
     import hashlib
 
     h = hashlib.sha1()
-    for f in ("k_tiled.cuh", "chambolle_math.cuh"):
+    for f in ("k_tiled.cuh", "chambolle_math.cuh", "k_step_coop.cuh"):
         with open(os.path.join(ROOT, "paper_2006_10004_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -362,47 +362,8 @@ def run_gb300(args):
 
     # ---- roofline of the dominant kernel: dual iterations timed alone -----------------------
     if args.workload != "config2":
-        H, W = job.f.shape
-        pitch = tv.pitch_for(W)
-        gl = torch.zeros((H, pitch), dtype=torch.float32, device=dev)
-        gl[:, :W] = torch.from_numpy(job.f / job.dt).to(dev)
-        p1 = torch.zeros_like(gl)
-        p2 = torch.zeros_like(gl)
-        iters = job.n_inner
-        plan.chambolle_iterate(gl, p1, p2, H, W, pitch, iters, stream=stream)  # tunes + warms
-        torch.cuda.synchronize()
-        s0 = plan.stats()
-        depth = max(1, s0["last_temporal_block"])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 5
-        e0.record(stream)
-        for _ in range(reps):
-            plan.chambolle_iterate(gl, p1, p2, H, W, pitch, iters, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        s1 = plan.stats()
-        n_launch = int(s1["kernel_launches"] - s0["kernel_launches"])
-        per_launch_s = e0.elapsed_time(e1) / 1000.0 / max(n_launch, 1)
-        # n_inner need not be a multiple of the temporal block (300 = 37 x 8 + 4): the bytes of
-        # an average launch are those of all iterations over all launches
-        alg_bytes = ALG_BYTES_FP32 * H * W * iters * reps / max(n_launch, 1)
-        achieved = alg_bytes / per_launch_s / 1e9
-        peak, src = _peaks()
-        traffic = None
-        tf = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tf):
-            try:
-                key = f"{wl.name}/tile{s1['last_tile']}/tb{depth}/{kernel_source_hash()}"
-                traffic = json.load(open(tf)).get(key)
-            except Exception:
-                traffic = None
-        result["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                              "frac": achieved / peak, "traffic": traffic,
-                              "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
-                              "kernel": "k_tiled", "per_launch_us": per_launch_s * 1e6,
-                              "temporal_block": depth,
-                              "iters_per_launch": iters * reps / max(n_launch, 1),
-                              "algorithmic_bytes_per_launch": alg_bytes}
+        result["roofline"], result["roofline_issue"] = measure_roofline(tv, torch, plan, wl.name, job,
+                                                                        dev, stream)
 
     # ---- CPU baseline: the FP64 oracle on this host -------------------------------------------
     if rank == 0 and not args.no_cpu_baseline and args.workload != "config2":
@@ -438,15 +399,19 @@ def run_gb300(args):
         ms = e0.elapsed_time(e1) / 3
         result["m1024"] = {"workload": syn.m1024.__doc__.strip().splitlines()[0], "decomps_per_s": 1000.0 / ms,
                            "ms_per_decomp": ms, "Mpx_iter_per_s": m.px_iters / ms / 1e3}
+        # the largest single-image workload (2048^2, K = 50, 500 iterations: its 80 MB dual state
+        # is 0.6 of the L2) with its own rooflines
+        result["config3"] = measure_decomposition(tv, torch, local, syn.config3(), dev, stream, flush)
         result["filter_bank_config1"] = measure_filters(tv, torch, plan, job, f_dev, stream, flush)
         result["inner_solvers"] = measure_solvers(tv, torch, plan, job, stream)
         result["acc_mode_compare"] = measure_acc_modes(tv, torch, local, job, f_dev, stream, flush)
         result["batched_config2"] = measure_batched(tv, torch, local, 2, 1)
         result["training_crops"] = measure_crops(tv, torch, local)
-        # one load the server keeps up with (latency) and one above its capacity (throughput)
+        # config 4's load points (20-200 req/s), each with a shortened request count
         rates = [float(x) for x in str(args.serve_rates).split(",")]
         pts = measure_serving(tv, local, rates, args.serve_requests)
         result["serving_config4"] = [{k: v for k, v in sv.items() if k != "clocks"} for sv in pts]
+        result["config"]["serving_requests_per_rate"] = args.serve_requests
 
     if rank == 0:
         print(json.dumps(result))
@@ -454,6 +419,117 @@ def run_gb300(args):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+SM_COUNT = 152          # GB300
+ISSUE_PER_SM_CLK = 4    # warp instructions issued per SM per clock (four schedulers)
+
+
+def _profile_record(key: str):
+    """The ncu record of a kernel launch (DRAM bytes, warp instructions, iterations of the
+    captured launch) from profiles/traffic.json, if one was taken of the current sources."""
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(tf)).get(key)
+    except Exception:
+        return None
+    return rec if isinstance(rec, dict) else None
+
+
+def measure_roofline(tv, torch, plan, wl_name, job, dev, stream, reps: int = 5):
+    """The dual-iteration kernel timed alone on the workload's image (per-launch duration by
+    CUDA events on the launch stream), against two ceilings:
+      hbm   -- algorithmic bytes (20 B per pixel-iteration: read p and g/lambda, write p) per
+               launch / duration, over the measured copy bandwidth; with temporal blocking
+               this can exceed 1 (the state is re-read from registers, not HBM);
+      issue -- warp instructions per launch (ncu count of the current sources, scaled by
+               iterations) / duration, over the SM count x 4 issue slots x the maximum clock.
+    `traffic` (DRAM bytes per launch) and the instruction count come from profiles/traffic.json
+    only while the kernel sources are those the capture was taken of."""
+    H, W = job.f.shape
+    pitch = tv.pitch_for(W)
+    gl = torch.zeros((H, pitch), dtype=torch.float32, device=dev)
+    gl[:, :W] = torch.from_numpy(job.f / job.dt).to(dev)
+    p1 = torch.zeros_like(gl)
+    p2 = torch.zeros_like(gl)
+    iters = job.n_inner
+    plan.chambolle_iterate(gl, p1, p2, H, W, pitch, iters, stream=stream)  # tunes + warms
+    torch.cuda.synchronize()
+    s0 = plan.stats()
+    depth = max(1, s0["last_temporal_block"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.chambolle_iterate(gl, p1, p2, H, W, pitch, iters, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s1 = plan.stats()
+    n_launch = max(int(s1["kernel_launches"] - s0["kernel_launches"]), 1)
+    per_launch_s = e0.elapsed_time(e1) / 1000.0 / n_launch
+    # n_inner need not be a multiple of the temporal block (300 = 37 x 8 + 4): an average
+    # launch does the iterations of all launches over their number
+    it_per_launch = iters * reps / n_launch
+    alg_bytes = ALG_BYTES_FP32 * H * W * it_per_launch
+    achieved = alg_bytes / per_launch_s / 1e9
+    peak, src = _peaks()
+    key = f"{wl_name}/tile{s1['last_tile']}/tb{depth}/{kernel_source_hash()}"
+    rec = _profile_record(key)
+    # DRAM bytes per launch (tile loads and stores: the same for a launch of fewer iterations)
+    traffic = rec.get("dram_bytes") if rec else None
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic,
+           "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+           "kernel": "k_tiled", "per_launch_us": per_launch_s * 1e6, "temporal_block": depth,
+           "iters_per_launch": it_per_launch, "algorithmic_bytes_per_launch": alg_bytes,
+           "profile_key": key}
+    issue = None
+    if rec and rec.get("warp_inst"):
+        mhz = _max_sm_mhz()
+        inst = rec["warp_inst"] * it_per_launch / rec.get("iters", it_per_launch)
+        ipeak = SM_COUNT * ISSUE_PER_SM_CLK * mhz * 1e6 / 1e9
+        ia = inst / per_launch_s / 1e9
+        issue = {"bound": "issue", "achieved": ia, "peak": ipeak, "unit": "Gwarp_inst/s", "frac": ia / ipeak,
+                 "peak_source": f"{SM_COUNT} SMs x {ISSUE_PER_SM_CLK} issue slots x {mhz:.0f} MHz (nominal)",
+                 "warp_inst_per_launch": inst,
+                 "thread_inst_per_px_iter": 32 * inst / (H * W * it_per_launch),
+                 "source": "ncu smsp__inst_executed.sum of the current sources (profiles/traffic.json)"}
+    return hbm, issue
+
+
+def _max_sm_mhz() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
+def measure_decomposition(tv, torch, local, wl, dev, stream, flush, steps: int = 5, warmup: int = 3):
+    """A second single-image workload of the default run: whole decompositions, device-timed
+    (L2 flushed before each), with the dual-iteration kernel's rooflines on the same image."""
+    job = wl.jobs[0]
+    with tv.Plan(local) as plan:
+        f_dev = torch.from_numpy(job.f).to(dev)
+        for _ in range(warmup):
+            plan.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream)
+        torch.cuda.synchronize()
+        ts = []
+        for i in range(steps):
+            flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.decompose(f_dev, job.dt, job.K, job.n_inner, job.edges, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        st = plan.stats()
+        ms = float(np.median(ts))
+        out = {"workload": wl.name, "H": job.f.shape[0], "W": job.f.shape[1], "K": job.K,
+               "n_inner": job.n_inner, "ms_per_decomp": ms, "Mpx_iter_per_s": job.px_iters / ms / 1e3,
+               "decomps_per_s": 1000.0 / ms, "tile": st["last_tile"], "temporal_block": st["last_temporal_block"],
+               "steps": steps, "l2": "flushed before every timed decomposition"}
+        out["roofline"], out["roofline_issue"] = measure_roofline(tv, torch, plan, wl.name, job, dev, stream)
+    return out
 
 
 def filter_bank(dt: float, K: int, n: int = 6):
@@ -906,8 +982,9 @@ def main():
     ap.add_argument("--ref-steps-k", type=int, default=6, help="ROF steps per reference-arm step")
     ap.add_argument("--quick", action="store_true",
                     help="skip the 1024^2, batched and serving summaries of the default run")
-    ap.add_argument("--serve-rates", default="50,100", help="config4 load points of the default run (req/s)")
-    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-rates", default="20,50,100,200", help="config4 load points of the default run (req/s)")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests per load point of the default run (config 4 specifies 2000)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the dual-iteration kernel on a --size x --size image")
     ap.add_argument("--size", type=int, default=4096)
