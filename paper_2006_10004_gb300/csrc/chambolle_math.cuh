@@ -95,15 +95,16 @@ __device__ __forceinline__ void tv_update_c(float &p1, float &p2, float &l1, flo
 // ---- the same arithmetic on two pixels at once (Blackwell packed f32x2 instructions) ----
 // Each lane of a packed operation rounds exactly like the scalar intrinsic above: a - b is
 // computed as fma(b, -1, a), which is the correctly rounded difference, and no packed product
-// feeds a packed sum (see sq_norm2). So tv_w2 / tv_update2 give the same bits as
+// feeds a packed sum (see sq_norm2). So tv_w2d / tv_update2 give the same bits as
 // tv_w / tv_update applied to .x and .y separately.
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 }
 
-__device__ __forceinline__ float2 tv_w2(float2 p1, float2 p1_up, float2 p2, float2 p2_left,
-                                        float2 gl) {
-    return sub2(__fadd2_rn(sub2(p1, p1_up), sub2(p2, p2_left)), gl);
+// tv_w on a pixel pair, with the column difference of p2 already formed (d2 = p2 - p2_left):
+// w = ((p1 - p1_up) + d2) - gl.
+__device__ __forceinline__ float2 tv_w2d(float2 p1, float2 p1_up, float2 d2, float2 gl) {
+    return sub2(__fadd2_rn(sub2(p1, p1_up), d2), gl);
 }
 
 // |G|^2 = G1*G1 + G2*G2 on a pixel pair: packed products, scalar sums. A product feeding a

@@ -89,8 +89,11 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
 #pragma unroll
             for (int j = 0; j < VP; ++j) {
                 const float2 p1u = (r == 0) ? up[j] : p1[r - 1][j];
-                const float2 p2l = make_float2(j == 0 ? left0 : p2[r][j - 1].y, p2[r][j].x);
-                w[r][j] = tv_w2(p1[r][j], p1u, p2[r][j], p2l, gl[r][j]);
+                // the column differences of p2 as two scalar differences (the same roundings
+                // as a packed difference with the left neighbours, without forming that pair)
+                const float2 d2 = make_float2(__fsub_rn(p2[r][j].x, j == 0 ? left0 : p2[r][j - 1].y),
+                                              __fsub_rn(p2[r][j].y, p2[r][j].x));
+                w[r][j] = tv_w2d(p1[r][j], p1u, d2, gl[r][j]);
             }
         }
         float2 dn[VP];
@@ -122,9 +125,9 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
 #pragma unroll
             for (int j = 0; j < VP; ++j) {
                 const float2 wd = (r < R - 1) ? w[r + 1][j] : dn[j];
-                const float2 wr = make_float2(w[r][j].y, j < VP - 1 ? w[r][j + 1].x : right_last);
                 float2 G1 = sub2(wd, w[r][j]);
-                float2 G2 = sub2(wr, w[r][j]);
+                float2 G2 = make_float2(__fsub_rn(w[r][j].y, w[r][j].x),
+                                        __fsub_rn(j < VP - 1 ? w[r][j + 1].x : right_last, w[r][j].y));
                 if (EDGE == kEdgeMasked) {
                     const int b0 = r * V + 2 * j;
                     G1.x = ((m1bits >> b0) & 1u) ? G1.x : 0.0f;
@@ -236,7 +239,12 @@ __device__ __forceinline__ bool tma_tile_load(const TmaMaps &tm, int xs, int ys,
 // is loaded by tma_tile_load from the maps tm (float32 p only). Float32 storage updates p with
 // the compensated form (hi + lo in registers, folded every kFold iterations); 16-bit storage
 // rounds p between launches anyway and updates it directly.
-template <int V, int R, int RW, int TB, typename P, bool FAST, bool TMA = false>
+// WAIT: the caller has neither waited for the preceding grid nor released the next one
+// (programmatic dependent launch). g/lambda, which no launch of a step writes, is then loaded
+// before the wait on every launch but a step's first (whose g/lambda the preceding epilogue
+// writes), and p after it. The next grid is released only after the wait: a grid released
+// earlier could start, and read g/lambda, while this one's predecessor still writes it.
+template <int V, int R, int RW, int TB, typename P, bool FAST, bool TMA = false, bool WAIT = false>
 __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int gstep, int blk,
                                            int depth, float tau, const TmaMaps *tm = nullptr) {
     static_assert(R * V <= 32, "mask bits");
@@ -285,6 +293,26 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
         static_assert(sizeof(P) == 4, "TMA tile loads read float32 p");
         if (!tma_tile_load<V, R, RW>(*tm, xs, ys, d.status, p1, p2, gl, lane, wy)) return;
     } else {
+        if (WAIT && blk == 0) {
+            pdl_wait();
+            pdl_trigger();
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = ry + r;
+            if (col_ok && y >= 0 && y < H) {
+                const FPack<V> c = *reinterpret_cast<const FPack<V> *>(ggl + (size_t)y * pitch + cx);
+#pragma unroll
+                for (int j = 0; j < VP; ++j) gl[r][j] = make_float2(c.v[2 * j], c.v[2 * j + 1]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < VP; ++j) gl[r][j] = make_float2(0.0f, 0.0f);
+            }
+        }
+        if (WAIT && blk != 0) {
+            pdl_wait();
+            pdl_trigger();
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int y = ry + r;
@@ -292,16 +320,14 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
                 const size_t off = (size_t)y * pitch + cx;
                 PPack<P, V> a = *reinterpret_cast<const PPack<P, V> *>(gp1 + off);
                 PPack<P, V> b = *reinterpret_cast<const PPack<P, V> *>(gp2 + off);
-                FPack<V> c = *reinterpret_cast<const FPack<V> *>(ggl + off);
 #pragma unroll
                 for (int j = 0; j < VP; ++j) {
                     p1[r][j] = make_float2(PStore<P>::load(a.v[2 * j]), PStore<P>::load(a.v[2 * j + 1]));
                     p2[r][j] = make_float2(PStore<P>::load(b.v[2 * j]), PStore<P>::load(b.v[2 * j + 1]));
-                    gl[r][j] = make_float2(c.v[2 * j], c.v[2 * j + 1]);
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < VP; ++j) p1[r][j] = p2[r][j] = gl[r][j] = make_float2(0.0f, 0.0f);
+                for (int j = 0; j < VP; ++j) p1[r][j] = p2[r][j] = make_float2(0.0f, 0.0f);
             }
         }
     }
@@ -380,10 +406,8 @@ template <int V, int R, int RW, int TB, int MINB, typename P, bool FAST>
 __global__ void __launch_bounds__(32 * RW, MINB)
     k_tiled_one(const __grid_constant__ ImgDesc d, int ntx, int gstep, int blk, int depth,
                 float tau) {
-    pdl_wait();
-    pdl_trigger();
     const int b = blockIdx.x;
-    tiled_tile<V, R, RW, TB, P, FAST>(d, b % ntx, b / ntx, gstep, blk, depth, tau);
+    tiled_tile<V, R, RW, TB, P, FAST, false, true>(d, b % ntx, b / ntx, gstep, blk, depth, tau);
 }
 
 // Single-image form with TMA tile loads (option `tma`; the shapes tma_shape_ok accepts).
@@ -428,7 +452,9 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     X(24, 2, 7, 8, 8, 1)         \
     X(25, 2, 8, 7, 8, 1)         \
     X(26, 2, 6, 8, 6, 1)         \
-    X(27, 2, 8, 6, 6, 1)
+    X(27, 2, 8, 6, 6, 1)         \
+    X(28, 2, 4, 14, 8, 0)        \
+    X(29, 2, 2, 28, 8, 0)
 
 using TiledKernel = void (*)(const TileRef *, const ImgDesc *, int, int, int, float);
 using TiledOneKernel = void (*)(const ImgDesc, int, int, int, int, float);
