@@ -738,6 +738,8 @@ def training_workload(n: int = 3000, size: int = 64, n_sources: int = 16, seed: 
 ALG_FLOPS_PER_PX_ITER = 17
 # float32 peak of the SMs: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# special-function (XU) pipe: 16 results per SM per clock (nominal) x 152 SMs x 2.07 GHz
+XU_PEAK_GOPS = 152 * 16 * 2.07e9 / 1e9
 
 
 def measure_crops(tv, torch, local, n: int = 3000, compare: bool = True, acc_mode: int = 0,
@@ -808,8 +810,16 @@ def run_training(args, tv, torch, local, ws):
               "gpu_launches": t["gpu_launches_per_call"] * t["steps"],
               "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "k_resident",
-                           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                           "peak_source": "nominal, not measured: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                            "algorithmic_flops_per_launch": flops},
+              # the square root and the reciprocal of every pixel-iteration run on the XU pipe
+              # (16 results per SM per clock, nominal): the second ceiling of this kernel
+              "roofline_xu": {"bound": "alu", "unit": "Gop/s", "kernel": "k_resident",
+                              "achieved": 2 * flops / ALG_FLOPS_PER_PX_ITER / (t["ms"] / 1e3) / 1e9,
+                              "peak": XU_PEAK_GOPS,
+                              "frac": 2 * flops / ALG_FLOPS_PER_PX_ITER / (t["ms"] / 1e3) / 1e9 / XU_PEAK_GOPS,
+                              "peak_source": "nominal, not measured: 152 SMs x 16 XU results per clock x 2.07 GHz",
+                              "ops_per_px_iter": 2},
               "clocks": clk.summary(), "training": m}
     print(json.dumps(result))
     return 0

@@ -1,6 +1,7 @@
 // Kernels around the hot loop: the reference one-iteration kernel, the start of a
 // decomposition, the per-step float64 epilogue and the standalone ROF helpers.
 #include <algorithm>
+#include <cstring>
 
 #include "chambolle_math.cuh"
 #include "epilogue.cuh"
@@ -194,23 +195,37 @@ __device__ __forceinline__ void epilogue_block(const ImgDesc &dd, int lb, int gs
 
 // Split epilogue (u in the three-buffer rotation, u_k in u_buf3(k)). First part: u_{k+1} and
 // g/dt of the next step; it is all the next step's dual iterations need.
-template <typename P>
+// WAIT: the caller has not yet waited for the preceding grid (programmatic dependent launch).
+// When the step ran dual iterations (which do not write u), u_k is then loaded before the wait
+// and p after it; with n_inner = 0 the preceding grid is the previous step's epilogue, which
+// writes u_k, so everything waits. The next grid is released after the wait.
+template <typename P, bool WAIT = false>
 __device__ __forceinline__ void epi_primal_block(const ImgDesc &d, int lb, int gstep, int depth) {
     const int k = gstep - d.s0;
-    if (k < 0 || k >= d.K) return;
     const int W = d.W;
     const int nbx = (W + kEpBlock - 1) / kEpBlock;
     const int i = lb / nbx;
     const int j = (lb % nbx) * kEpBlock + threadIdx.x;
-    if (j >= W) return;
+    const bool live = k >= 0 && k < d.K && j < W;
     const size_t n = (size_t)i * W + j;
+    double uc = 0.0;  // u_k: a float64 value, or a (hi, lo) float pair in the same 8 bytes
+    const bool early = WAIT && d.n_inner > 0;
+    if (live && early) uc = u_buf3(d, k)[n];
+    if (WAIT) {
+        pdl_wait();
+        pdl_trigger();
+    }
+    if (!live) return;
+    if (!early) uc = u_buf3(d, k)[n];
     const DivTerms dv = step_div_terms<P>(d, k, i, j, depth);
     float gl_next;
     if (d.acc_mode) {
-        const ff un = epi_primal<FFOps>(d, k, n, dv, FFOps::load(u_buf3(d, k), n), &gl_next);
+        ff ucf;
+        memcpy(&ucf, &uc, sizeof(ucf));
+        const ff un = epi_primal<FFOps>(d, k, n, dv, ucf, &gl_next);
         FFOps::store(u_buf3(d, k + 1), n, un);
     } else {
-        const double un = epi_primal<F64Ops>(d, k, n, dv, F64Ops::load(u_buf3(d, k), n), &gl_next);
+        const double un = epi_primal<F64Ops>(d, k, n, dv, uc, &gl_next);
         F64Ops::store(u_buf3(d, k + 1), n, un);
     }
     d.gl[(size_t)i * d.pitch + j] = gl_next;
@@ -250,9 +265,7 @@ __global__ void __launch_bounds__(kEpBlock)
 template <typename P>
 __global__ void __launch_bounds__(kEpBlock)
     k_epi_primal_one(const __grid_constant__ ImgDesc d, int gstep, int depth) {
-    pdl_wait();
-    pdl_trigger();
-    epi_primal_block<P>(d, blockIdx.x, gstep, depth);
+    epi_primal_block<P, true>(d, blockIdx.x, gstep, depth);
 }
 
 __global__ void __launch_bounds__(kEpBlock)
