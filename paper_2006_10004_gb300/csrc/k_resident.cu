@@ -85,7 +85,11 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     __shared__ __align__(16) float s_p1b[RW][TW];
     __shared__ __align__(16) float s_wt[RW][TW];
     __shared__ double s_part[TH];
-    extern __shared__ double s_phi[];  // H * W values of |phi_k| [, H * W values of phi_k f]
+    // dynamic shared memory: g/dt of the tile (TH x TW floats; the registers stay free for p and
+    // its low parts), then H * W values of |phi_k| [and H * W values of phi_k f]
+    extern __shared__ double s_dyn[];
+    float *s_gl = reinterpret_cast<float *>(s_dyn);
+    double *s_phi = s_dyn + (size_t)TH * TW / 2;
 
     const ImgDesc &d = descs[idx[blockIdx.x]];
     const int H = d.H, W = d.W, pitch = d.pitch;
@@ -118,13 +122,15 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     }
 
     // u_0 = f (Eq. TVflow), g/dt of step 0, p = 0
-    float2 p1[R][VP], p2[R][VP], gl[R][VP];
+    float2 p1[R][VP], p2[R][VP];
     float2 l1[R][VP], l2[R][VP];  // low parts of p (zero between steps: a step ends at a fold point)
+    float *my_gl = s_gl + (size_t)ry * TW + cx;  // this thread's pixels in s_gl (row stride TW)
+    const GlShared gl{my_gl, TW};
 #pragma unroll
     for (int r = 0; r < R; ++r) {
 #pragma unroll
         for (int j = 0; j < VP; ++j) {
-            p1[r][j] = p2[r][j] = gl[r][j] = make_float2(0.0f, 0.0f);
+            p1[r][j] = p2[r][j] = make_float2(0.0f, 0.0f);
             l1[r][j] = l2[r][j] = make_float2(0.0f, 0.0f);
             float g2[2] = {0.0f, 0.0f};
 #pragma unroll
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(32 * RW, MINB)
                     if (d.u_trace) d.u_trace[n] = (double)fv;
                 }
             }
-            gl[r][j] = make_float2(g2[0], g2[1]);
+            *reinterpret_cast<float2 *>(my_gl + r * TW + 2 * j) = make_float2(g2[0], g2[1]);
         }
     }
 
@@ -161,11 +167,11 @@ __global__ void __launch_bounds__(32 * RW, MINB)
         }
         __syncthreads();
         if (exact)  // the image fills the tile: masks only on its last row and column
-            tiled_iterate<V, R, RW, FAST, kEdgeExact, true, true>(p1, p2, l1, l2, gl, d.n_inner, 0,
+            tiled_iterate_g<V, R, RW, FAST, kEdgeExact, true, true>(p1, p2, l1, l2, gl, d.n_inner, 0,
                                                                   d.n_inner, tau, 0u, 0u,
                                                             s_p1b, s_wt, lane, wy);
         else
-            tiled_iterate<V, R, RW, FAST, kEdgeMasked, true, true>(p1, p2, l1, l2, gl, d.n_inner, 0,
+            tiled_iterate_g<V, R, RW, FAST, kEdgeMasked, true, true>(p1, p2, l1, l2, gl, d.n_inner, 0,
                                                                    d.n_inner, tau, m1, m2,
                                                              s_p1b, s_wt, lane, wy);
         // p to global for the divergence's neighbours
@@ -191,7 +197,8 @@ __global__ void __launch_bounds__(32 * RW, MINB)
         for (int r = 0; r < R; ++r) {
 #pragma unroll
             for (int j = 0; j < VP; ++j) {
-                float g2[2] = {gl[r][j].x, gl[r][j].y};
+                const float2 gcur = gl(r, j);
+                float g2[2] = {gcur.x, gcur.y};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int y = ry + r, c = cx + 2 * j + h;
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(32 * RW, MINB)
                         if (d.S_par) s_phif[(size_t)y * W + c] = pf;
                     }
                 }
-                gl[r][j] = make_float2(g2[0], g2[1]);
+                *reinterpret_cast<float2 *>(my_gl + r * TW + 2 * j) = make_float2(g2[0], g2[1]);
             }
         }
         __syncthreads();
@@ -246,11 +253,11 @@ static const ResidentVariant kResident[] = {
 };
 #undef TVSPEC_RESIDENT
 static constexpr int kNumResident = (int)(sizeof(kResident) / sizeof(kResident[0]));
-// The compensated update keeps two more floats per pixel in registers: the 16-pixel layouts
-// budgeted for 3 or 4 CTAs per SM spill heavily (measured on 3000 crops of 64^2, K = 50, 300
-// iterations: 3.7 k / 2.8 k crops/s), the 512-thread 8-pixel layout does not (13.5 k crops/s,
-// as the 2-CTA 16-pixel layout).
-static const int kAutoOrder[] = {4, 1, 2};
+// The compensated update keeps two more floats per pixel in registers, so g/dt lives in shared
+// memory here. Measured on 3000 crops of 64^2 (K = 50, 300 iterations): the 256-thread,
+// 16-pixel layout at 2 CTAs per SM 16.6 k crops/s, the 512-thread 8-pixel layouts 12.8 k (1 CTA
+// per SM) and 15.4 k (2), the 16-pixel layouts budgeted for 3 or 4 CTAs per SM spill (4.7 k).
+static const int kAutoOrder[] = {3, 1, 2};
 
 static bool resident_holds(int i, int H, int W) {
     return W <= 32 * kResident[i].V && H <= kResident[i].RW * kResident[i].R;
@@ -280,7 +287,8 @@ cudaError_t launch_resident(int variant, bool fast, const ImgDesc *descs, const 
     if (variant < 0 || variant >= kNumResident) return cudaErrorInvalidValue;
     const ResidentVariant &v = kResident[variant];
     const ResidentKernel k = fast ? v.fast : v.ieee;
-    const size_t smem = (size_t)(32 * v.V) * (v.RW * v.R) * sizeof(double) * (parseval ? 2 : 1);
+    const size_t tile = (size_t)(32 * v.V) * (v.RW * v.R);
+    const size_t smem = tile * sizeof(float) + tile * sizeof(double) * (parseval ? 2 : 1);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<n, 32 * v.RW, smem, st>>>(descs, idx, tau, warm_start);

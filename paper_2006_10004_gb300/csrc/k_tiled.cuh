@@ -61,13 +61,30 @@ constexpr int kEdgeNone = 0, kEdgeMasked = 1, kEdgeExact = 2;
 // folded at the fold points (kFold); the launch covers iterations [it0, it0 + n_iter) of a step
 // of n_total, with it0 a fold point, so l1 / l2 start and end at zero. Otherwise l1 / l2 are not
 // touched.
-template <int V, int R, int RW, bool FAST, int EDGE, bool ZERO_LEFT = false, bool COMP = false>
-__device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
-                                              float2 (&l1)[R][V / 2], float2 (&l2)[R][V / 2],
-                                              const float2 (&gl)[R][V / 2], int n_iter, int it0,
-                                              int n_total, float tau, unsigned m1bits, unsigned m2bits,
-                                              float (*s_p1b)[32 * V], float (*s_wt)[32 * V],
-                                              int lane, int wy) {
+// g/lambda of a thread's pixel pairs, read by gl(r, j): held in registers (GlRegs), or in
+// shared memory (GlShared: the thread's rows of a tile-sized array, for kernels that keep the
+// registers for p).
+template <int R, int VP>
+struct GlRegs {
+    const float2 (&a)[R][VP];
+    __device__ __forceinline__ float2 operator()(int r, int j) const { return a[r][j]; }
+};
+struct GlShared {
+    const float *base;  // the thread's first pixel: row ry, column lane * V of the tile
+    int stride;         // floats per tile row
+    __device__ __forceinline__ float2 operator()(int r, int j) const {
+        return *reinterpret_cast<const float2 *>(base + r * stride + 2 * j);
+    }
+};
+
+template <int V, int R, int RW, bool FAST, int EDGE, bool ZERO_LEFT = false, bool COMP = false,
+          class GL>
+__device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
+                                                float2 (&l1)[R][V / 2], float2 (&l2)[R][V / 2],
+                                                const GL &gl, int n_iter, int it0, int n_total,
+                                                float tau, unsigned m1bits, unsigned m2bits,
+                                                float (*s_p1b)[32 * V], float (*s_wt)[32 * V],
+                                                int lane, int wy) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int VP = V / 2;
     float2 w[R][VP];
@@ -93,7 +110,7 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
                 // as a packed difference with the left neighbours, without forming that pair)
                 const float2 d2 = make_float2(__fsub_rn(p2[r][j].x, j == 0 ? left0 : p2[r][j - 1].y),
                                               __fsub_rn(p2[r][j].y, p2[r][j].x));
-                w[r][j] = tv_w2d(p1[r][j], p1u, d2, gl[r][j]);
+                w[r][j] = tv_w2d(p1[r][j], p1u, d2, gl(r, j));
             }
         }
         float2 dn[VP];
@@ -167,6 +184,18 @@ __device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p
             __syncthreads();
         }
     }
+}
+
+template <int V, int R, int RW, bool FAST, int EDGE, bool ZERO_LEFT = false, bool COMP = false>
+__device__ __forceinline__ void tiled_iterate(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
+                                              float2 (&l1)[R][V / 2], float2 (&l2)[R][V / 2],
+                                              const float2 (&gl)[R][V / 2], int n_iter, int it0,
+                                              int n_total, float tau, unsigned m1bits, unsigned m2bits,
+                                              float (*s_p1b)[32 * V], float (*s_wt)[32 * V],
+                                              int lane, int wy) {
+    tiled_iterate_g<V, R, RW, FAST, EDGE, ZERO_LEFT, COMP>(
+        p1, p2, l1, l2, GlRegs<R, V / 2>{gl}, n_iter, it0, n_total, tau, m1bits, m2bits, s_p1b,
+        s_wt, lane, wy);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
