@@ -357,6 +357,15 @@ def test_config1_full_size_parity(plan):
     print("config1", m)
 
 
+def test_config1_full_size_cold_start_parity(tv):
+    # p restarted from zero at every ROF step (the warm_start = 0 option), the whole config-1 run
+    job = syn.config1().jobs[0]
+    with tv.Plan(0, warm_start=0) as p:
+        g = p.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True)
+    ref = oracle.decompose(job.f, job.dt, job.K, job.n_inner, job.edges, trace=True, warm_start=False)
+    print("config1 cold start", assert_parity(g, ref, job.f, "config1 cold start"))
+
+
 def test_m1024_full_size_parity_as_benchmarked(plan):
     # the 1024^2 workload of the decompositions/s figure, whole (K=50, 300 iterations), from
     # device memory on a side stream as the bench runs it
