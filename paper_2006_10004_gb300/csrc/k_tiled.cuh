@@ -15,10 +15,14 @@
 //     shared-memory rows per warp (the bottom row of p1, the top row of w), with two CTA
 //     barriers per iteration.
 //
-// Image borders: pixels outside the image are loaded as zero and their gradient is masked to
-// zero, so p stays zero there; this realises p1_{-1,j} = p2_{i,-1} = 0. The gradient is also
-// masked on the last image row (G1) and column (G2): the Neumann boundary. Tiles that do not
-// touch a border skip all masks.
+// Image borders. Where the tiles are edge-aligned (tile_span: no tile reaches past the image),
+// a tile on the left border sets p2_{i,-1} = 0 for its first column, one on the bottom border
+// G1 = 0 on its last row and one on the right border G2 = 0 on its last column (the Neumann
+// boundary); p1_{-1,j} = 0 holds for every tile's first row, whose upper neighbour is taken as
+// zero. Otherwise pixels outside the image are loaded as zero and their gradient is masked to
+// zero, so p stays zero there, which realises p1_{-1,j} = p2_{i,-1} = 0, and the gradient is
+// masked on the last image row (G1) and column (G2). Tiles that touch none of the borders that
+// need a condition skip all of them.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (a plain struct; no driver call in device code)
@@ -51,7 +55,13 @@ struct alignas(sizeof(float) * V) FPack {
 //               on the last row and G2 on the last column, nothing else is masked. The same
 //               values as kEdgeMasked with the masks of that image, with a select per row
 //               instead of four per pixel pair.
-constexpr int kEdgeNone = 0, kEdgeMasked = 1, kEdgeExact = 2;
+//   kEdgeClamp  an edge-aligned tile on one or more image borders; m1bits holds this thread's
+//               flags: kClampLeft (lane 0 of a tile on the left border: p2_{i,-1} = 0),
+//               kClampRight (lane 31 on the right border: G2 = 0 on the last column),
+//               kClampBottom (the last warp on the bottom border: G1 = 0 on the last row).
+//               The same values as kEdgeMasked on the image's pixels.
+constexpr int kEdgeNone = 0, kEdgeMasked = 1, kEdgeExact = 2, kEdgeClamp = 3;
+constexpr unsigned kClampLeft = 1u, kClampRight = 2u, kClampBottom = 4u;
 
 // The iterations of one launch on the registers of one thread. Pixels are processed in
 // horizontal pairs (columns 2q, 2q+1 of the lane) with packed f32x2 arithmetic.
@@ -103,6 +113,7 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
         for (int r = 0; r < R; ++r) {
             float left0 = __shfl_up_sync(FULL, p2[r][VP - 1].y, 1);
             if (ZERO_LEFT && lane == 0) left0 = 0.0f;
+            if (EDGE == kEdgeClamp && (m1bits & kClampLeft)) left0 = 0.0f;
 #pragma unroll
             for (int j = 0; j < VP; ++j) {
                 const float2 p1u = (r == 0) ? up[j] : p1[r - 1][j];
@@ -154,6 +165,9 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
                 } else if (EDGE == kEdgeExact) {
                     if (r == R - 1 && wy == RW - 1) G1 = make_float2(0.0f, 0.0f);  // last row
                     if (j == VP - 1 && lane == 31) G2.y = 0.0f;                    // last column
+                } else if (EDGE == kEdgeClamp) {
+                    if (r == R - 1 && (m1bits & kClampBottom)) G1 = make_float2(0.0f, 0.0f);
+                    if (j == VP - 1 && (m1bits & kClampRight)) G2.y = 0.0f;
                 }
                 if constexpr (COMP)
                     tv_update2_c<FAST>(p1[r][j], p2[r][j], l1[r][j], l2[r][j], G1, G2, tau);
@@ -303,8 +317,10 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
 
     const int lane = threadIdx.x & 31;
     const int wy = threadIdx.x >> 5;
-    const int x0 = tx * OW, y0 = ty * OH;
-    const int xs = x0 - HX, ys = y0 - TB;
+    const bool aligned = tiles_edge_aligned(H, W, TH, TW, V);
+    const TileSpan spx = tile_span(tx, tile_count(W, TW, OW, aligned), W, TW, HX, OW, aligned);
+    const TileSpan spy = tile_span(ty, tile_count(H, TH, OH, aligned), H, TH, TB, OH, aligned);
+    const int xs = spx.s, ys = spy.s;
     const int cx = xs + lane * V;
     const int ry = ys + wy * R;
     const bool col_ok = (cx >= 0) && (cx < pitch);
@@ -371,11 +387,20 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
         __syncthreads();
     }
 
-    const bool interior = ys >= 0 && ys + TH <= H - 1 && xs >= 0 && xs + TW <= W - 1;
+    // (a tile on the top border needs no condition: its first row's upper neighbour is zero)
+    const bool interior = aligned ? !(spx.first || spx.last || spy.last)
+                                  : ys >= 0 && ys + TH <= H - 1 && xs >= 0 && xs + TW <= W - 1;
     if (interior) {
         tiled_iterate<V, R, RW, FAST, kEdgeNone, false, COMP>(p1, p2, l1, l2, gl, n_iter, blk * depth,
                                                               d.n_inner, tau, 0u, 0u, s_p1b, s_wt,
                                                               lane, wy);
+    } else if (aligned) {
+        const unsigned flags = (spx.first && lane == 0 ? kClampLeft : 0u) |
+                               (spx.last && lane == 31 ? kClampRight : 0u) |
+                               (spy.last && wy == RW - 1 ? kClampBottom : 0u);
+        tiled_iterate<V, R, RW, FAST, kEdgeClamp, false, COMP>(p1, p2, l1, l2, gl, n_iter, blk * depth,
+                                                               d.n_inner, tau, flags, 0u, s_p1b,
+                                                               s_wt, lane, wy);
     } else {
         unsigned m1 = 0u, m2 = 0u;
 #pragma unroll
@@ -396,11 +421,11 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
 
     // store the exact centre into the other copy (the halo this CTA read belongs to other
     // tiles' centres, which they write into that copy too, never into the one being read)
-    if (cx >= x0 && cx < x0 + OW && cx < W) {
+    if (cx >= spx.a && cx < spx.b) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int y = ry + r;
-            if (y >= y0 && y < y0 + OH && y < H) {
+            if (y >= spy.a && y < spy.b) {
                 const size_t off = (size_t)y * pitch + cx;
                 PPack<P, V> a, b;
 #pragma unroll

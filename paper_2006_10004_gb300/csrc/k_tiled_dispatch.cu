@@ -87,8 +87,9 @@ cudaError_t launch_tiled(int shape, int p_storage, bool fast, const TileRef *til
 bool tiled_one_available(int p_storage) { return p_storage == 0; }
 
 // ---- TMA tile loads --------------------------------------------------------------------------
-// Shapes with a TMA kernel: every tile's first column xs = tx * OW - HX is a multiple of 4
-// floats (the 16-byte rule of a tiled TMA copy; OW and HX multiples of 4), and the three
+// Shapes with a TMA kernel: every tile's first column (tx * OW - HX, or tx * OW and W - TW for
+// edge-aligned tiles) is a multiple of 4 floats (the 16-byte rule of a tiled TMA copy; OW and HX
+// multiples of 4, and W for edge-aligned tiles, checked at launch), and the three
 // TH x TW tiles plus the exchange rows fit the 48 KB of static shared memory.
 #define TVSPEC_TMA_SHAPES(X) X(8, 2, 8, 4, 4, 0) X(24, 2, 7, 8, 8, 1) X(25, 2, 8, 7, 8, 1)
 
@@ -146,12 +147,15 @@ static cudaError_t encode_map(CUtensorMap *m, const void *base, const ImgDesc &d
 cudaError_t launch_tiled_one(int shape, int p_storage, bool fast, const ImgDesc &d, int gstep,
                              int blk, int depth, float tau, cudaStream_t st, bool pdl, bool tma) {
     if (shape < 0 || shape >= tiled_shape_count() || p_storage != 0) return cudaErrorInvalidValue;
-    const bool use_tma = tma && tma_shape_ok(shape, p_storage);
     TiledOneKernel k = tiled_one_kernel_f32(shape, fast);
     if (!k) return cudaErrorInvalidValue;
-    int ow, oh;
-    tiled_output_tile(kShapes[shape], &ow, &oh);
-    const int ntx = (d.W + ow - 1) / ow, nty = (d.H + oh - 1) / oh;
+    int ntx, nty;
+    tiles_for(shape, d.H, d.W, &ntx, &nty);
+    // edge-aligned tiles: the last column of tiles starts at W - TW, a multiple of 4 floats
+    // only when W is
+    const TileShape &s = kShapes[shape];
+    const bool aligned = tiles_edge_aligned(d.H, d.W, s.RW * s.R, 32 * s.V, s.V);
+    const bool use_tma = tma && tma_shape_ok(shape, p_storage) && (!aligned || d.W % 4 == 0);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ntx * nty));
     cfg.blockDim = dim3((unsigned)(32 * kShapes[shape].RW));

@@ -366,10 +366,12 @@ void LaunchSet::release() {
 }
 
 void tiles_for(int shape, int H, int W, int *ntx, int *nty) {
+    const TileShape s = tiled_shape(shape);
     int ow, oh;
-    tiled_output_tile(tiled_shape(shape), &ow, &oh);
-    *ntx = (W + ow - 1) / ow;
-    *nty = (H + oh - 1) / oh;
+    tiled_output_tile(s, &ow, &oh);
+    const bool aligned = tiles_edge_aligned(H, W, s.RW * s.R, 32 * s.V, s.V);
+    *ntx = tile_count(W, 32 * s.V, ow, aligned);
+    *nty = tile_count(H, s.RW * s.R, oh, aligned);
 }
 
 template <typename T>

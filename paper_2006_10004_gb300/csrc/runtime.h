@@ -104,8 +104,6 @@ struct LaunchSet {
 // Builds and uploads (synchronously) the tables for descs with tile shape `shape` (-1: none).
 tvspec_status launchset_build(LaunchSet *ls, const std::vector<ImgDesc> &descs, int shape,
                               int depth);
-// Tiles of one image for a shape: (ceil(W/ow), ceil(H/oh)).
-void tiles_for(int shape, int H, int W, int *ntx, int *nty);
 
 struct CacheEntry {
     std::string key;

@@ -82,6 +82,47 @@ __host__ __device__ __forceinline__ int launches_per_step(int n_inner, int depth
     return (n_inner + depth - 1) / depth;
 }
 
+// Placement of the tiled kernel's tiles along one image axis of n pixels, for a tile of T
+// pixels with a halo of h on each side (centre c = T - 2h):
+//  * edge-aligned, when the image is at least one tile long in both directions and its width a
+//    multiple of the columns per lane V: tile t < m - 1 reads [t c, t c + T) and the last one
+//    [n - T, n); tile 0 stores [0, c + h), tile t [t c + h, (t + 1) c + h), the last
+//    [(m - 1) c + h, n). No tile reaches past the image, so the border conditions reduce to a
+//    few selects on the tile's first column and last row and column, instead of per-pixel
+//    masks; every stored pixel lies at least h from the edges of its tile that are not image
+//    borders, so it is exact after up to h iterations;
+//  * otherwise: tile t reads [t c - h, t c + c + h) and stores [t c, t c + c); the pixels
+//    outside the image are masked.
+__host__ __device__ __forceinline__ bool tiles_edge_aligned(int H, int W, int TH, int TW, int V) {
+    return H >= TH && W >= TW && W % V == 0;
+}
+__host__ __device__ __forceinline__ int tile_count(int n, int T, int c, bool aligned) {
+    return aligned ? 1 + (n - T + c - 1) / c : (n + c - 1) / c;
+}
+struct TileSpan {
+    int s;       // first pixel the tile reads
+    int a, b;    // pixels [a, b) the tile stores
+    bool first;  // the tile starts at the image's first pixel (edge-aligned placement)
+    bool last;   // the tile ends at the image's last pixel (edge-aligned placement)
+};
+__host__ __device__ __forceinline__ TileSpan tile_span(int t, int m, int n, int T, int h, int c,
+                                                       bool aligned) {
+    TileSpan sp;
+    if (aligned) {
+        sp.first = t == 0;
+        sp.last = t == m - 1;
+        sp.s = sp.last ? n - T : t * c;
+        sp.a = sp.first ? 0 : t * c + h;
+        sp.b = sp.last ? n : (t + 1) * c + h;
+    } else {
+        sp.first = sp.last = false;
+        sp.s = t * c - h;
+        sp.a = t * c;
+        sp.b = t * c + c < n ? t * c + c : n;
+    }
+    return sp;
+}
+
 // One tile of the tiled dual-iteration kernel: image index and tile coordinates.
 struct TileRef {
     int img;
@@ -127,6 +168,9 @@ int tiled_shape_count();
 TileShape tiled_shape(int index);
 // Output tile (columns, rows) of a shape: (32 V - 2 roundup(TB, V), RW R - 2 TB).
 void tiled_output_tile(const TileShape &s, int *ow, int *oh);
+// Tiles of one image for a shape along x and y (tile_count, edge-aligned where
+// tiles_edge_aligned allows).
+void tiles_for(int shape, int H, int W, int *ntx, int *nty);
 
 // Launch one tiled pass of global step gstep: every CTA advances its tile by
 // min(depth, n_inner - blk depth) iterations (depth <= the shape's TB), reading copy

@@ -92,8 +92,12 @@ def test_band_edges_not_covering_time_range(plan):
 # ---------------------------------------------------------------------------------------------
 # bit-identity of the implementation choices
 # ---------------------------------------------------------------------------------------------
-def test_every_tile_shape_and_depth_bit_identical(tv):
-    f = _img(100, 150, 7)
+# 100 x 150: edge-aligned tiles for the V = 2 shapes up to 100 rows, masked ones for V = 4 (150
+# is not a multiple of 4) and the taller shapes; 120 x 200: edge-aligned for V = 2 and V = 4;
+# 56 x 64: exactly one tile of the 64 x 56 shapes (all four borders in one tile)
+@pytest.mark.parametrize("H,W", [(100, 150), (120, 200), (56, 64)])
+def test_every_tile_shape_and_depth_bit_identical(tv, H, W):
+    f = _img(H, W, 7 + H)
     args = (f, 0.5, 4, 23, syn.DYADIC_EDGES)
     with tv.Plan(0, kernel=tv.KERNEL_NAIVE) as p:
         base = p.decompose(*args, trace=True)
