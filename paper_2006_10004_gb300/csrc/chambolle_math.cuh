@@ -30,16 +30,23 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// w_ij = (div p)_ij - g_ij / lambda with
+// The iteration works on wn = -tau w, where w_ij = (div p)_ij - g_ij / lambda and
 //   (div p)_ij = (p1_ij - p1_{i-1,j}) + (p2_ij - p2_{i,j-1}),
-// where p1_{-1,j} = p2_{i,-1} = 0 and p1 on the last row / p2 on the last column are zero
-// (the kernels keep them zero), which makes div the negative adjoint of the forward gradient.
-__device__ __forceinline__ float tv_w(float p1, float p1_up, float p2, float p2_left, float gl) {
-    return __fsub_rn(__fadd_rn(__fsub_rn(p1, p1_up), __fsub_rn(p2, p2_left)), gl);
+// with p1_{-1,j} = p2_{i,-1} = 0 and p1 on the last row / p2 on the last column zero (the
+// kernels keep them zero), which makes div the negative adjoint of the forward gradient. The
+// forward differences of wn are then na = -tau G directly, the quantity the update needs, so
+// no per-pixel product by tau remains in the loop. wn is formed with one rounding from the
+// divergence and glt = tau g/lambda (each kernel multiplies g/lambda by tau once, when it loads
+// it): wn = fma(div p, -tau, glt). For tau a power of two (1/8 by default) scaling by tau is
+// exact, so wn = -tau w and na = -tau G to the bit, as if w and G were formed first.
+__device__ __forceinline__ float tv_wn(float p1, float p1_up, float p2, float p2_left, float glt,
+                                       float tau) {
+    return __fmaf_rn(__fadd_rn(__fsub_rn(p1, p1_up), __fsub_rn(p2, p2_left)), -tau, glt);
 }
 
 // p <- (p + tau G) / (1 + tau |G|), |G| = sqrt(G1^2 + G2^2)  (isotropic; Eq. TV's pointwise
-// Euclidean norm), evaluated in float32 as an increment:
+// Euclidean norm), evaluated in float32 as an increment from na = -tau G (the differences of
+// wn above):
 //   a = tau G,  x = |a| = tau |G|,  s = 1 / (1 + x),  p <- p + (a - p x) s.
 // The result is the same real number; the order of the float32 roundings is what differs.
 // Forming 1 + tau|G| and p + tau G first rounds away whatever of tau|G| and tau G lies below
@@ -53,10 +60,9 @@ __device__ __forceinline__ float tv_w(float p1, float p1_up, float p2, float p2_
 // arithmetic gives the same errors against the float64 oracle with exact and with 2-ulp
 // one-sided biased square root and reciprocal). Signs are arranged so that no negation is
 // needed: na = -a, nden = -(1 + x), ns = 1 / nden, u = p x + na = -(a - p x), and u ns is the
-// increment. For tau a power of two (1/8 by default) na is exact.
+// increment.
 template <bool FAST>
-__device__ __forceinline__ void tv_update(float &p1, float &p2, float G1, float G2, float tau) {
-    const float na1 = __fmul_rn(-tau, G1), na2 = __fmul_rn(-tau, G2);
+__device__ __forceinline__ void tv_update(float &p1, float &p2, float na1, float na2) {
     const float n2 = __fadd_rn(__fmul_rn(na1, na1), __fmul_rn(na2, na2));
     const float x = FAST ? sqrt_approx(n2) : __fsqrt_rn(n2);
     const float nden = __fsub_rn(-1.0f, x);
@@ -76,9 +82,8 @@ __device__ __forceinline__ void tv_update(float &p1, float &p2, float G1, float 
 // one float per component between launches (measured on that workload: u 2.6e-5, bands
 // 1.2e-4 max|f|). w and the epilogue use hi.
 template <bool FAST>
-__device__ __forceinline__ void tv_update_c(float &p1, float &p2, float &l1, float &l2, float G1,
-                                            float G2, float tau) {
-    const float na1 = __fmul_rn(-tau, G1), na2 = __fmul_rn(-tau, G2);
+__device__ __forceinline__ void tv_update_c(float &p1, float &p2, float &l1, float &l2, float na1,
+                                            float na2) {
     const float n2 = __fadd_rn(__fmul_rn(na1, na1), __fmul_rn(na2, na2));
     const float x = FAST ? sqrt_approx(n2) : __fsqrt_rn(n2);
     const float nden = __fsub_rn(-1.0f, x);
@@ -95,33 +100,31 @@ __device__ __forceinline__ void tv_update_c(float &p1, float &p2, float &l1, flo
 // ---- the same arithmetic on two pixels at once (Blackwell packed f32x2 instructions) ----
 // Each lane of a packed operation rounds exactly like the scalar intrinsic above: a - b is
 // computed as fma(b, -1, a), which is the correctly rounded difference, and no packed product
-// feeds a packed sum (see sq_norm2). So tv_w2d / tv_update2 give the same bits as
-// tv_w / tv_update applied to .x and .y separately.
+// feeds a packed sum (see sq_norm2). So tv_wn2d / tv_update2 give the same bits as
+// tv_wn / tv_update applied to .x and .y separately.
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 }
 
-// tv_w on a pixel pair, with the column difference of p2 already formed (d2 = p2 - p2_left):
-// w = ((p1 - p1_up) + d2) - gl.
-__device__ __forceinline__ float2 tv_w2d(float2 p1, float2 p1_up, float2 d2, float2 gl) {
-    return sub2(__fadd2_rn(sub2(p1, p1_up), d2), gl);
+// tv_wn on a pixel pair, with the column difference of p2 already formed (d2 = p2 - p2_left):
+// wn = fma((p1 - p1_up) + d2, -tau, glt), ntau2 = (-tau, -tau).
+__device__ __forceinline__ float2 tv_wn2d(float2 p1, float2 p1_up, float2 d2, float2 glt,
+                                          float2 ntau2) {
+    return __ffma2_rn(__fadd2_rn(sub2(p1, p1_up), d2), ntau2, glt);
 }
 
-// |G|^2 = G1*G1 + G2*G2 on a pixel pair: packed products, scalar sums. A product feeding a
+// |a|^2 = a1*a1 + a2*a2 on a pixel pair: packed products, scalar sums. A product feeding a
 // sum may be fused into one multiply-add by the compiler when both are packed; with the sums
 // done by the scalar rounded addition each lane equals the scalar
-// __fadd_rn(__fmul_rn(G1, G1), __fmul_rn(G2, G2)), which the tests check bit for bit.
-__device__ __forceinline__ float2 sq_norm2(float2 G1, float2 G2) {
-    const float2 a = __fmul2_rn(G1, G1);
-    const float2 b = __fmul2_rn(G2, G2);
+// __fadd_rn(__fmul_rn(a1, a1), __fmul_rn(a2, a2)), which the tests check bit for bit.
+__device__ __forceinline__ float2 sq_norm2(float2 a1, float2 a2) {
+    const float2 a = __fmul2_rn(a1, a1);
+    const float2 b = __fmul2_rn(a2, a2);
     return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
 }
 
 template <bool FAST>
-__device__ __forceinline__ void tv_update2(float2 &p1, float2 &p2, float2 G1, float2 G2,
-                                           float tau) {
-    const float2 nt2 = make_float2(-tau, -tau);
-    const float2 na1 = __fmul2_rn(nt2, G1), na2 = __fmul2_rn(nt2, G2);
+__device__ __forceinline__ void tv_update2(float2 &p1, float2 &p2, float2 na1, float2 na2) {
     const float2 n2 = sq_norm2(na1, na2);
     float2 x;
     x.x = FAST ? sqrt_approx(n2.x) : __fsqrt_rn(n2.x);
@@ -146,9 +149,7 @@ __device__ __forceinline__ void tv_fold2(float2 &p, float2 &l) {
 
 template <bool FAST>
 __device__ __forceinline__ void tv_update2_c(float2 &p1, float2 &p2, float2 &l1, float2 &l2,
-                                             float2 G1, float2 G2, float tau) {
-    const float2 nt2 = make_float2(-tau, -tau);
-    const float2 na1 = __fmul2_rn(nt2, G1), na2 = __fmul2_rn(nt2, G2);
+                                             float2 na1, float2 na2) {
     const float2 n2 = sq_norm2(na1, na2);
     float2 x;
     x.x = FAST ? sqrt_approx(n2.x) : __fsqrt_rn(n2.x);

@@ -27,19 +27,20 @@ __global__ void __launch_bounds__(256)
     if (i >= H || j >= W) return;
     auto P1 = [&](int y, int x) { return PStore<P>::load(p1i[(size_t)y * pitch + x]); };
     auto P2 = [&](int y, int x) { return PStore<P>::load(p2i[(size_t)y * pitch + x]); };
-    auto w_at = [&](int y, int x) {
+    // wn = -tau w at a pixel; its forward differences are na = -tau G
+    auto wn_at = [&](int y, int x) {
         const float p1u = y > 0 ? P1(y - 1, x) : 0.0f;
         const float p2l = x > 0 ? P2(y, x - 1) : 0.0f;
-        return tv_w(P1(y, x), p1u, P2(y, x), p2l, gl[(size_t)y * pitch + x]);
+        return tv_wn(P1(y, x), p1u, P2(y, x), p2l, __fmul_rn(tau, gl[(size_t)y * pitch + x]), tau);
     };
-    const float w = w_at(i, j);
-    const float G1 = (i < H - 1) ? __fsub_rn(w_at(i + 1, j), w) : 0.0f;
-    const float G2 = (j < W - 1) ? __fsub_rn(w_at(i, j + 1), w) : 0.0f;
+    const float wn = wn_at(i, j);
+    const float na1 = (i < H - 1) ? __fsub_rn(wn_at(i + 1, j), wn) : 0.0f;
+    const float na2 = (j < W - 1) ? __fsub_rn(wn_at(i, j + 1), wn) : 0.0f;
     float a = P1(i, j), b = P2(i, j);
     const size_t o = (size_t)i * pitch + j;
     if constexpr (sizeof(P) == 4) {
         float la = it % kFold != 0 ? q1i[o] : 0.0f, lb = it % kFold != 0 ? q2i[o] : 0.0f;
-        tv_update_c<FAST>(a, b, la, lb, G1, G2, tau);
+        tv_update_c<FAST>(a, b, la, lb, na1, na2);
         if ((it + 1) % kFold == 0 || it + 1 == n_total) {
             tv_fold(a, la);
             tv_fold(b, lb);
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(256)
         q1o[o] = la;
         q2o[o] = lb;
     } else {
-        tv_update<FAST>(a, b, G1, G2, tau);
+        tv_update<FAST>(a, b, na1, na2);
     }
     p1o[o] = PStore<P>::store(a);
     p2o[o] = PStore<P>::store(b);

@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     __shared__ __align__(16) float s_p1b[RW][TW];
     __shared__ __align__(16) float s_wt[RW][TW];
     __shared__ double s_part[TH];
-    // dynamic shared memory: g/dt of the tile (TH x TW floats; the registers stay free for p and
-    // its low parts), then H * W values of |phi_k| [and H * W values of phi_k f]
+    // dynamic shared memory: tau g/dt of the tile (TH x TW floats; the registers stay free for p
+    // and its low parts), then H * W values of |phi_k| [and H * W values of phi_k f]
     extern __shared__ double s_dyn[];
     float *s_gl = reinterpret_cast<float *>(s_dyn);
     double *s_phi = s_dyn + (size_t)TH * TW / 2;
@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(32 * RW, MINB)
                     if (d.u_trace) d.u_trace[n] = (double)fv;
                 }
             }
-            *reinterpret_cast<float2 *>(my_gl + r * TW + 2 * j) = make_float2(g2[0], g2[1]);
+            *reinterpret_cast<float2 *>(my_gl + r * TW + 2 * j) =
+                make_float2(__fmul_rn(tau, g2[0]), __fmul_rn(tau, g2[1]));  // tau g/dt
         }
     }
 
@@ -156,16 +157,7 @@ __global__ void __launch_bounds__(32 * RW, MINB)
                 for (int j = 0; j < VP; ++j)
                     p1[r][j] = p2[r][j] = l1[r][j] = l2[r][j] = make_float2(0.0f, 0.0f);
         }
-        if (RW > 1) {
-            FPack<V> q;
-#pragma unroll
-            for (int j = 0; j < VP; ++j) {
-                q.v[2 * j] = p1[R - 1][j].x;
-                q.v[2 * j + 1] = p1[R - 1][j].y;
-            }
-            *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
-        }
-        __syncthreads();
+        __syncthreads();  // tau g/dt of the step in s_gl; the exchange rows free
         if (exact)  // the image fills the tile: masks only on its last row and column
             tiled_iterate_g<V, R, RW, FAST, kEdgeExact, true, true>(p1, p2, l1, l2, gl, d.n_inner, 0,
                                                                   d.n_inner, tau, 0u, 0u,
@@ -214,7 +206,8 @@ __global__ void __launch_bounds__(32 * RW, MINB)
                         if (d.S_par) s_phif[(size_t)y * W + c] = pf;
                     }
                 }
-                *reinterpret_cast<float2 *>(my_gl + r * TW + 2 * j) = make_float2(g2[0], g2[1]);
+                *reinterpret_cast<float2 *>(my_gl + r * TW + 2 * j) =
+                    make_float2(__fmul_rn(tau, g2[0]), __fmul_rn(tau, g2[1]));  // tau g/dt
             }
         }
         __syncthreads();

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(32 * RW, MINB)
             for (int j = 0; j < VP; ++j) {
                 p1[r][j] = make_float2(a.v[2 * j], a.v[2 * j + 1]);
                 p2[r][j] = make_float2(b.v[2 * j], b.v[2 * j + 1]);
-                gl[r][j] = make_float2(c.v[2 * j], c.v[2 * j + 1]);
+                gl[r][j] = __fmul2_rn(make_float2(tau, tau), make_float2(c.v[2 * j], c.v[2 * j + 1]));
             }
         } else {
 #pragma unroll
@@ -145,16 +145,6 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     }
 
     for (int blk = 0; blk < nb; ++blk) {
-        if (RW > 1) {
-            FPack<V> q;
-#pragma unroll
-            for (int j = 0; j < VP; ++j) {
-                q.v[2 * j] = p1[R - 1][j].x;
-                q.v[2 * j + 1] = p1[R - 1][j].y;
-            }
-            *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
-            __syncthreads();
-        }
         const int n_iter = min(min(depth, TB), d.n_inner - blk * depth);
         if (interior)
             tiled_iterate<V, R, RW, FAST, kEdgeNone, false, true>(p1, p2, l1, l2, gl, n_iter,
@@ -314,7 +304,7 @@ __global__ void __launch_bounds__(32 * RW, MINB)
             for (int j = 0; j < VP; ++j) {
                 p1[r][j] = make_float2(a.v[2 * j], a.v[2 * j + 1]);
                 p2[r][j] = make_float2(b.v[2 * j], b.v[2 * j + 1]);
-                gl[r][j] = make_float2(c.v[2 * j], c.v[2 * j + 1]);
+                gl[r][j] = __fmul2_rn(make_float2(tau, tau), make_float2(c.v[2 * j], c.v[2 * j + 1]));
             }
         } else {
 #pragma unroll
@@ -342,16 +332,6 @@ __global__ void __launch_bounds__(32 * RW, MINB)
     }
 
     for (int blk = 0; blk < nb; ++blk) {
-        if (RW > 1) {
-            FPack<V> q;
-#pragma unroll
-            for (int j = 0; j < VP; ++j) {
-                q.v[2 * j] = p1[R - 1][j].x;
-                q.v[2 * j + 1] = p1[R - 1][j].y;
-            }
-            *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
-            __syncthreads();
-        }
         const int n_iter = min(min(depth, TB), d.n_inner - blk * depth);
         if (interior)
             tiled_iterate<V, R, RW, FAST, kEdgeNone, false, true>(p1, p2, l1, l2, gl, n_iter,

@@ -71,9 +71,9 @@ constexpr unsigned kClampLeft = 1u, kClampRight = 2u, kClampBottom = 4u;
 // folded at the fold points (kFold); the launch covers iterations [it0, it0 + n_iter) of a step
 // of n_total, with it0 a fold point, so l1 / l2 start and end at zero. Otherwise l1 / l2 are not
 // touched.
-// g/lambda of a thread's pixel pairs, read by gl(r, j): held in registers (GlRegs), or in
-// shared memory (GlShared: the thread's rows of a tile-sized array, for kernels that keep the
-// registers for p).
+// tau g/lambda of a thread's pixel pairs (glt of tv_wn), read by gl(r, j): held in registers
+// (GlRegs), or in shared memory (GlShared: the thread's rows of a tile-sized array, for kernels
+// that keep the registers for p). Kernels multiply g/lambda by tau as they load it.
 template <int R, int VP>
 struct GlRegs {
     const float2 (&a)[R][VP];
@@ -87,6 +87,16 @@ struct GlShared {
     }
 };
 
+// Row exchange between the warps of a CTA. Warp wy needs p1 of the last row of warp wy - 1
+// (for the divergence of its first row) and wn of the first row of warp wy + 1 (for the
+// gradient of its last row); its other rows need only its own registers. So each iteration
+// computes wn on rows 1..R-1 first, then on row 0 with p1 from above, and hands its wn row 0
+// up; it updates rows 0..R-2 first, then row R-1 with wn from below, and hands its p1 row R-1
+// down; two CTA barriers per iteration order the hand-offs. (Measured: this order is faster
+// than rows in sequence, and faster than pairwise named barriers between neighbouring warps,
+// which let a warp wait for its neighbours only.) The function writes its first hand-off row
+// itself; callers separate two calls by a CTA barrier (the exchange rows are reused). A call
+// with n_iter <= 0 does nothing.
 template <int V, int R, int RW, bool FAST, int EDGE, bool ZERO_LEFT = false, bool COMP = false,
           class GL>
 __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
@@ -97,84 +107,101 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
                                                 int lane, int wy) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int VP = V / 2;
-    float2 w[R][VP];
+    if (n_iter <= 0) return;  // uniform over the CTA
+    const float2 ntau2 = make_float2(-tau, -tau);
+    float2 w[R][VP];  // wn = -tau (div p - g/lambda)
+
+    auto put_row = [&](float *dst, const float2 (&v)[VP]) {
+        FPack<V> q;
+#pragma unroll
+        for (int j = 0; j < VP; ++j) {
+            q.v[2 * j] = v[j].x;
+            q.v[2 * j + 1] = v[j].y;
+        }
+        *reinterpret_cast<FPack<V> *>(dst + lane * V) = q;
+    };
+    auto get_row = [&](const float *src, float2 (&v)[VP]) {
+        const FPack<V> q = *reinterpret_cast<const FPack<V> *>(src + lane * V);
+#pragma unroll
+        for (int j = 0; j < VP; ++j) v[j] = make_float2(q.v[2 * j], q.v[2 * j + 1]);
+    };
+    // wn = -tau w on row r, with p1 of the row above in upv
+    auto wn_row = [&](int r, const float2 (&upv)[VP]) {
+        float left0 = __shfl_up_sync(FULL, p2[r][VP - 1].y, 1);
+        if (ZERO_LEFT && lane == 0) left0 = 0.0f;
+        if (EDGE == kEdgeClamp && (m1bits & kClampLeft)) left0 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < VP; ++j) {
+            // the column differences of p2 as two scalar differences (the same roundings as a
+            // packed difference with the left neighbours, without forming that pair)
+            const float2 d2 = make_float2(__fsub_rn(p2[r][j].x, j == 0 ? left0 : p2[r][j - 1].y),
+                                          __fsub_rn(p2[r][j].y, p2[r][j].x));
+            w[r][j] = tv_wn2d(p1[r][j], upv[j], d2, gl(r, j), ntau2);
+        }
+    };
+    // p <- (p + tau grad w) / (1 + tau |grad w|) on row r from na = grad wn = -tau grad w, with
+    // wn of the row below in wdv
+    auto update_row = [&](int r, const float2 (&wdv)[VP]) {
+        const float right_last = __shfl_down_sync(FULL, w[r][0].x, 1);
+#pragma unroll
+        for (int j = 0; j < VP; ++j) {
+            float2 na1 = sub2(wdv[j], w[r][j]);
+            float2 na2 = make_float2(__fsub_rn(w[r][j].y, w[r][j].x),
+                                     __fsub_rn(j < VP - 1 ? w[r][j + 1].x : right_last, w[r][j].y));
+            if (EDGE == kEdgeMasked) {
+                const int b0 = r * V + 2 * j;
+                na1.x = ((m1bits >> b0) & 1u) ? na1.x : 0.0f;
+                na1.y = ((m1bits >> (b0 + 1)) & 1u) ? na1.y : 0.0f;
+                na2.x = ((m2bits >> b0) & 1u) ? na2.x : 0.0f;
+                na2.y = ((m2bits >> (b0 + 1)) & 1u) ? na2.y : 0.0f;
+            } else if (EDGE == kEdgeExact) {
+                if (r == R - 1 && wy == RW - 1) na1 = make_float2(0.0f, 0.0f);  // last row
+                if (j == VP - 1 && lane == 31) na2.y = 0.0f;                    // last column
+            } else if (EDGE == kEdgeClamp) {
+                if (r == R - 1 && (m1bits & kClampBottom)) na1 = make_float2(0.0f, 0.0f);
+                if (j == VP - 1 && (m1bits & kClampRight)) na2.y = 0.0f;
+            }
+            if constexpr (COMP)
+                tv_update2_c<FAST>(p1[r][j], p2[r][j], l1[r][j], l2[r][j], na1, na2);
+            else
+                tv_update2<FAST>(p1[r][j], p2[r][j], na1, na2);
+        }
+    };
+
+    // p1 of the last row for the warp below, as of the call's start
+    if (RW > 1) {
+        put_row(s_p1b[wy], p1[R - 1]);
+        __syncthreads();
+    }
     for (int it = 0; it < n_iter; ++it) {
-        // ---- w = div p - g/lambda on every owned pixel
+        // ---- wn on rows 1..R-1, then on row 0 with p1 from the warp above (zero above the
+        // tile's first row: a halo row, or the image's p1_{-1,j} = 0)
+#pragma unroll
+        for (int r = 1; r < R; ++r) wn_row(r, p1[r - 1]);
         float2 up[VP];
         if (RW > 1 && wy > 0) {
-            FPack<V> q = *reinterpret_cast<const FPack<V> *>(&s_p1b[wy - 1][lane * V]);
-#pragma unroll
-            for (int j = 0; j < VP; ++j) up[j] = make_float2(q.v[2 * j], q.v[2 * j + 1]);
+            get_row(s_p1b[wy - 1], up);
         } else {
 #pragma unroll
-            for (int j = 0; j < VP; ++j) up[j] = make_float2(0.0f, 0.0f);  // tile top row: halo
+            for (int j = 0; j < VP; ++j) up[j] = make_float2(0.0f, 0.0f);
         }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float left0 = __shfl_up_sync(FULL, p2[r][VP - 1].y, 1);
-            if (ZERO_LEFT && lane == 0) left0 = 0.0f;
-            if (EDGE == kEdgeClamp && (m1bits & kClampLeft)) left0 = 0.0f;
-#pragma unroll
-            for (int j = 0; j < VP; ++j) {
-                const float2 p1u = (r == 0) ? up[j] : p1[r - 1][j];
-                // the column differences of p2 as two scalar differences (the same roundings
-                // as a packed difference with the left neighbours, without forming that pair)
-                const float2 d2 = make_float2(__fsub_rn(p2[r][j].x, j == 0 ? left0 : p2[r][j - 1].y),
-                                              __fsub_rn(p2[r][j].y, p2[r][j].x));
-                w[r][j] = tv_w2d(p1[r][j], p1u, d2, gl(r, j));
-            }
-        }
-        float2 dn[VP];
+        wn_row(0, up);
         if (RW > 1) {
-            FPack<V> q;
-#pragma unroll
-            for (int j = 0; j < VP; ++j) {
-                q.v[2 * j] = w[0][j].x;
-                q.v[2 * j + 1] = w[0][j].y;
-            }
-            *reinterpret_cast<FPack<V> *>(&s_wt[wy][lane * V]) = q;
+            put_row(s_wt[wy], w[0]);
             __syncthreads();
-            if (wy < RW - 1) {
-                FPack<V> b = *reinterpret_cast<const FPack<V> *>(&s_wt[wy + 1][lane * V]);
+        }
+        // ---- the update on rows 0..R-2, then on row R-1 with wn from the warp below (the
+        // tile's last row: a halo row, or the image's last row, whose G1 is masked)
 #pragma unroll
-                for (int j = 0; j < VP; ++j) dn[j] = make_float2(b.v[2 * j], b.v[2 * j + 1]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < VP; ++j) dn[j] = w[R - 1][j];  // tile bottom row: halo
-            }
+        for (int r = 0; r < R - 1; ++r) update_row(r, w[r + 1]);
+        float2 dn[VP];
+        if (RW > 1 && wy < RW - 1) {
+            get_row(s_wt[wy + 1], dn);
         } else {
 #pragma unroll
             for (int j = 0; j < VP; ++j) dn[j] = w[R - 1][j];
         }
-        // ---- p <- (p + tau grad w) / (1 + tau |grad w|)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float right_last = __shfl_down_sync(FULL, w[r][0].x, 1);
-#pragma unroll
-            for (int j = 0; j < VP; ++j) {
-                const float2 wd = (r < R - 1) ? w[r + 1][j] : dn[j];
-                float2 G1 = sub2(wd, w[r][j]);
-                float2 G2 = make_float2(__fsub_rn(w[r][j].y, w[r][j].x),
-                                        __fsub_rn(j < VP - 1 ? w[r][j + 1].x : right_last, w[r][j].y));
-                if (EDGE == kEdgeMasked) {
-                    const int b0 = r * V + 2 * j;
-                    G1.x = ((m1bits >> b0) & 1u) ? G1.x : 0.0f;
-                    G1.y = ((m1bits >> (b0 + 1)) & 1u) ? G1.y : 0.0f;
-                    G2.x = ((m2bits >> b0) & 1u) ? G2.x : 0.0f;
-                    G2.y = ((m2bits >> (b0 + 1)) & 1u) ? G2.y : 0.0f;
-                } else if (EDGE == kEdgeExact) {
-                    if (r == R - 1 && wy == RW - 1) G1 = make_float2(0.0f, 0.0f);  // last row
-                    if (j == VP - 1 && lane == 31) G2.y = 0.0f;                    // last column
-                } else if (EDGE == kEdgeClamp) {
-                    if (r == R - 1 && (m1bits & kClampBottom)) G1 = make_float2(0.0f, 0.0f);
-                    if (j == VP - 1 && (m1bits & kClampRight)) G2.y = 0.0f;
-                }
-                if constexpr (COMP)
-                    tv_update2_c<FAST>(p1[r][j], p2[r][j], l1[r][j], l2[r][j], G1, G2, tau);
-                else
-                    tv_update2<FAST>(p1[r][j], p2[r][j], G1, G2, tau);
-            }
-        }
+        update_row(R - 1, dn);
         if constexpr (COMP) {
             const int done = it0 + it + 1;  // iterations of the step completed
             if (done % kFold == 0 || done == n_total) {  // uniform over the CTA
@@ -187,14 +214,8 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
                     }
             }
         }
-        if (RW > 1) {
-            FPack<V> q;
-#pragma unroll
-            for (int j = 0; j < VP; ++j) {
-                q.v[2 * j] = p1[R - 1][j].x;
-                q.v[2 * j + 1] = p1[R - 1][j].y;
-            }
-            *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
+        if (RW > 1 && it + 1 < n_iter) {  // (after the last iteration no one reads it)
+            put_row(s_p1b[wy], p1[R - 1]);
             __syncthreads();
         }
     }
@@ -376,15 +397,12 @@ __device__ __forceinline__ void tiled_tile(const ImgDesc &d, int tx, int ty, int
             }
         }
     }
-    if (RW > 1) {
-        FPack<V> q;
+    {
+        const float2 tau2 = make_float2(tau, tau);  // glt = tau g/lambda, once per launch
 #pragma unroll
-        for (int j = 0; j < VP; ++j) {
-            q.v[2 * j] = p1[R - 1][j].x;
-            q.v[2 * j + 1] = p1[R - 1][j].y;
-        }
-        *reinterpret_cast<FPack<V> *>(&s_p1b[wy][lane * V]) = q;
-        __syncthreads();
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < VP; ++j) gl[r][j] = __fmul2_rn(tau2, gl[r][j]);
     }
 
     // (a tile on the top border needs no condition: its first row's upper neighbour is zero)
