@@ -71,31 +71,31 @@ __device__ __forceinline__ void tv_update(float &p1, float &p2, float na1, float
     p2 = __fmaf_rn(__fmaf_rn(p2, x, na2), ns, p2);
 }
 
-// The same update with p held as an unevaluated sum hi + lo of two floats (p1 + l1, p2 + l2):
-// the increment plus the carried remainder, d = u ns + lo, is added to hi, and what of d the
-// sum could not hold stays in lo (Fast2Sum: lo = d - ((hi + d) - hi); exact when |hi| >= |d|, a
-// close approximation otherwise). Increments of a slowly converging pixel are often smaller
-// than half an ulp of p; rounded into p alone they vanish, always in the same direction, and
-// over the 25 000 dual iterations of a 2048^2 decomposition (K = 50 steps of 500) that alone
-// puts u at 1.5e-4 max|f| and the bands at 1.2e-3 max|f| from the float64 oracle, past the
-// accuracy target. lo is folded into hi (tv_fold) every kFold iterations, so p is stored as
-// one float per component between launches (measured on that workload: u 2.6e-5, bands
-// 1.2e-4 max|f|). w and the epilogue use hi.
+// The same update with p held as an unevaluated sum hi + lo of two floats. hi stays fixed
+// between fold points; lo accumulates the increments, lo <- lo + u ns in one fused operation;
+// the iteration reads the working value p = fl(hi + lo) (tv_pval), for w and for the update
+// alike. At the fold points, every kFold iterations of a step and after its last, hi <- p and
+// lo <- 0, so p is stored as one float per component between launches. Increments of a slowly
+// converging pixel are often smaller than half an ulp of p; rounded into p alone they vanish,
+// always in the same direction, and over the 25 000 dual iterations of a 2048^2 decomposition
+// (K = 50 steps of 500) that alone puts u at 1.5e-4 max|f| and the bands at 1.2e-3 max|f|
+// from the float64 oracle, past the accuracy target. Here they are added to lo, whose ulp is
+// far below p's, and reach p through the rounding of hi + lo, so only what is left below half
+// an ulp of p at a fold point is lost. (Against carrying the remainder by Fast2Sum after each
+// increment it needs one rounded addition per iteration instead of three: p = fl(hi + lo) is
+// the rounded sum that Fast2Sum would also leave in hi.)
 template <bool FAST>
-__device__ __forceinline__ void tv_update_c(float &p1, float &p2, float &l1, float &l2, float na1,
-                                            float na2) {
+__device__ __forceinline__ void tv_update_acc(float p1, float p2, float &l1, float &l2, float na1,
+                                              float na2) {
     const float n2 = __fadd_rn(__fmul_rn(na1, na1), __fmul_rn(na2, na2));
     const float x = FAST ? sqrt_approx(n2) : __fsqrt_rn(n2);
     const float nden = __fsub_rn(-1.0f, x);
     const float ns = FAST ? rcp_approx(nden) : __frcp_rn(nden);
-    const float d1 = __fmaf_rn(__fmaf_rn(p1, x, na1), ns, l1);
-    const float d2 = __fmaf_rn(__fmaf_rn(p2, x, na2), ns, l2);
-    const float h1 = __fadd_rn(p1, d1), h2 = __fadd_rn(p2, d2);
-    l1 = __fsub_rn(d1, __fsub_rn(h1, p1));
-    l2 = __fsub_rn(d2, __fsub_rn(h2, p2));
-    p1 = h1;
-    p2 = h2;
+    l1 = __fmaf_rn(__fmaf_rn(p1, x, na1), ns, l1);
+    l2 = __fmaf_rn(__fmaf_rn(p2, x, na2), ns, l2);
 }
+// The working value of a compensated component: p = fl(hi + lo).
+__device__ __forceinline__ float tv_pval(float hi, float lo) { return __fadd_rn(hi, lo); }
 
 // ---- the same arithmetic on two pixels at once (Blackwell packed f32x2 instructions) ----
 // Each lane of a packed operation rounds exactly like the scalar intrinsic above: a - b is
@@ -137,19 +137,10 @@ __device__ __forceinline__ void tv_update2(float2 &p1, float2 &p2, float2 na1, f
     p2 = __ffma2_rn(__ffma2_rn(p2, x, na2), ns, p2);
 }
 
-// The fold points of the compensated update: the remainder goes into p with one rounding.
-__device__ __forceinline__ void tv_fold(float &p, float &l) {
-    p = __fadd_rn(p, l);
-    l = 0.0f;
-}
-__device__ __forceinline__ void tv_fold2(float2 &p, float2 &l) {
-    p = __fadd2_rn(p, l);
-    l = make_float2(0.0f, 0.0f);
-}
-
+// tv_update_acc on a pixel pair: only lo changes; the caller refreshes p = hi + lo (packed).
 template <bool FAST>
-__device__ __forceinline__ void tv_update2_c(float2 &p1, float2 &p2, float2 &l1, float2 &l2,
-                                             float2 na1, float2 na2) {
+__device__ __forceinline__ void tv_update2_acc(float2 p1, float2 p2, float2 &l1, float2 &l2,
+                                               float2 na1, float2 na2) {
     const float2 n2 = sq_norm2(na1, na2);
     float2 x;
     x.x = FAST ? sqrt_approx(n2.x) : __fsqrt_rn(n2.x);
@@ -158,13 +149,8 @@ __device__ __forceinline__ void tv_update2_c(float2 &p1, float2 &p2, float2 &l1,
     float2 ns;
     ns.x = FAST ? rcp_approx(nden.x) : __frcp_rn(nden.x);
     ns.y = FAST ? rcp_approx(nden.y) : __frcp_rn(nden.y);
-    const float2 d1 = __ffma2_rn(__ffma2_rn(p1, x, na1), ns, l1);
-    const float2 d2 = __ffma2_rn(__ffma2_rn(p2, x, na2), ns, l2);
-    const float2 h1 = __fadd2_rn(p1, d1), h2 = __fadd2_rn(p2, d2);
-    l1 = sub2(d1, sub2(h1, p1));
-    l2 = sub2(d2, sub2(h2, p2));
-    p1 = h1;
-    p2 = h2;
+    l1 = __ffma2_rn(__ffma2_rn(p1, x, na1), ns, l1);
+    l2 = __ffma2_rn(__ffma2_rn(p2, x, na2), ns, l2);
 }
 
 }  // namespace tvspec

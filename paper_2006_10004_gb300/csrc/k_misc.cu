@@ -15,7 +15,8 @@ namespace tvspec {
 // ---------------------------------------------------------------------------------------------
 // Float32 storage: p is updated in the compensated form as hi + lo, with lo carried between
 // launches in q1 / q2 (in -> out) and folded into hi at the fold points (kFold), exactly as the
-// tiled kernels do in registers; `it` is the iteration's index within the step of n_total.
+// tiled kernels do in registers; `it` is the iteration's index within the step of n_total. hi
+// (p1 / p2) changes only at the fold points.
 template <typename P, bool FAST>
 __global__ void __launch_bounds__(256)
     k_naive(const P *__restrict__ p1i, const P *__restrict__ p2i, P *__restrict__ p1o,
@@ -27,11 +28,22 @@ __global__ void __launch_bounds__(256)
     if (i >= H || j >= W) return;
     auto P1 = [&](int y, int x) { return PStore<P>::load(p1i[(size_t)y * pitch + x]); };
     auto P2 = [&](int y, int x) { return PStore<P>::load(p2i[(size_t)y * pitch + x]); };
+    // float32 storage: p1 / p2 hold hi, q1 / q2 lo (zero at a fold point, where the previous
+    // launch folded it into hi); the iteration reads the working value fl(hi + lo)
+    const bool carry = sizeof(P) == 4 && it % kFold != 0;
+    auto V1 = [&](int y, int x) {
+        const float h = P1(y, x);
+        return carry ? tv_pval(h, q1i[(size_t)y * pitch + x]) : h;
+    };
+    auto V2 = [&](int y, int x) {
+        const float h = P2(y, x);
+        return carry ? tv_pval(h, q2i[(size_t)y * pitch + x]) : h;
+    };
     // wn = -tau w at a pixel; its forward differences are na = -tau G
     auto wn_at = [&](int y, int x) {
-        const float p1u = y > 0 ? P1(y - 1, x) : 0.0f;
-        const float p2l = x > 0 ? P2(y, x - 1) : 0.0f;
-        return tv_wn(P1(y, x), p1u, P2(y, x), p2l, __fmul_rn(tau, gl[(size_t)y * pitch + x]), tau);
+        const float p1u = y > 0 ? V1(y - 1, x) : 0.0f;
+        const float p2l = x > 0 ? V2(y, x - 1) : 0.0f;
+        return tv_wn(V1(y, x), p1u, V2(y, x), p2l, __fmul_rn(tau, gl[(size_t)y * pitch + x]), tau);
     };
     const float wn = wn_at(i, j);
     const float na1 = (i < H - 1) ? __fsub_rn(wn_at(i + 1, j), wn) : 0.0f;
@@ -39,11 +51,12 @@ __global__ void __launch_bounds__(256)
     float a = P1(i, j), b = P2(i, j);
     const size_t o = (size_t)i * pitch + j;
     if constexpr (sizeof(P) == 4) {
-        float la = it % kFold != 0 ? q1i[o] : 0.0f, lb = it % kFold != 0 ? q2i[o] : 0.0f;
-        tv_update_c<FAST>(a, b, la, lb, na1, na2);
-        if ((it + 1) % kFold == 0 || it + 1 == n_total) {
-            tv_fold(a, la);
-            tv_fold(b, lb);
+        float la = carry ? q1i[o] : 0.0f, lb = carry ? q2i[o] : 0.0f;
+        tv_update_acc<FAST>(carry ? tv_pval(a, la) : a, carry ? tv_pval(b, lb) : b, la, lb, na1, na2);
+        if ((it + 1) % kFold == 0 || it + 1 == n_total) {  // fold: hi <- fl(hi + lo), lo <- 0
+            a = tv_pval(a, la);
+            b = tv_pval(b, lb);
+            la = lb = 0.0f;
         }
         q1o[o] = la;
         q2o[o] = lb;

@@ -67,10 +67,11 @@ constexpr unsigned kClampLeft = 1u, kClampRight = 2u, kClampBottom = 4u;
 // horizontal pairs (columns 2q, 2q+1 of the lane) with packed f32x2 arithmetic.
 // ZERO_LEFT: the tile's first column is the image's first column (no halo), so lane 0's left
 // neighbour p2_{i,-1} is 0 rather than a halo value.
-// COMP (float32 storage): p is held as hi + lo (p1 + l1, p2 + l2), updated by tv_update2_c and
-// folded at the fold points (kFold); the launch covers iterations [it0, it0 + n_iter) of a step
-// of n_total, with it0 a fold point, so l1 / l2 start and end at zero. Otherwise l1 / l2 are not
-// touched.
+// COMP (float32 storage): p is held as hi + lo (tv_update_acc): p1 / p2 carry the working
+// value fl(hi + lo), l1 / l2 the low parts, and hi lives in this function; at the fold points
+// (kFold) hi <- p, lo <- 0. The launch covers iterations [it0, it0 + n_iter) of a step of
+// n_total, with it0 a fold point, so l1 / l2 start and end at zero and p = hi on entry and exit.
+// Otherwise l1 / l2 are not touched.
 // tau g/lambda of a thread's pixel pairs (glt of tv_wn), read by gl(r, j): held in registers
 // (GlRegs), or in shared memory (GlShared: the thread's rows of a tile-sized array, for kernels
 // that keep the registers for p). Kernels multiply g/lambda by tau as they load it.
@@ -110,6 +111,16 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
     if (n_iter <= 0) return;  // uniform over the CTA
     const float2 ntau2 = make_float2(-tau, -tau);
     float2 w[R][VP];  // wn = -tau (div p - g/lambda)
+    float2 h1[R][VP], h2[R][VP];  // hi of the compensated form (COMP)
+    if constexpr (COMP) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int j = 0; j < VP; ++j) {
+                h1[r][j] = p1[r][j];
+                h2[r][j] = p2[r][j];
+            }
+    }
 
     auto put_row = [&](float *dst, const float2 (&v)[VP]) {
         FPack<V> q;
@@ -161,10 +172,13 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
                 if (r == R - 1 && (m1bits & kClampBottom)) na1 = make_float2(0.0f, 0.0f);
                 if (j == VP - 1 && (m1bits & kClampRight)) na2.y = 0.0f;
             }
-            if constexpr (COMP)
-                tv_update2_c<FAST>(p1[r][j], p2[r][j], l1[r][j], l2[r][j], na1, na2);
-            else
+            if constexpr (COMP) {
+                tv_update2_acc<FAST>(p1[r][j], p2[r][j], l1[r][j], l2[r][j], na1, na2);
+                p1[r][j] = __fadd2_rn(h1[r][j], l1[r][j]);  // the row's new working value
+                p2[r][j] = __fadd2_rn(h2[r][j], l2[r][j]);
+            } else {
                 tv_update2<FAST>(p1[r][j], p2[r][j], na1, na2);
+            }
         }
     };
 
@@ -208,9 +222,10 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
 #pragma unroll
                 for (int r = 0; r < R; ++r)
 #pragma unroll
-                    for (int j = 0; j < VP; ++j) {
-                        tv_fold2(p1[r][j], l1[r][j]);
-                        tv_fold2(p2[r][j], l2[r][j]);
+                    for (int j = 0; j < VP; ++j) {  // hi <- fl(hi + lo) = p, lo <- 0
+                        h1[r][j] = p1[r][j];
+                        h2[r][j] = p2[r][j];
+                        l1[r][j] = l2[r][j] = make_float2(0.0f, 0.0f);
                     }
             }
         }
