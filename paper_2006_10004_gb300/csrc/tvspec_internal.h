@@ -8,10 +8,10 @@
 
 namespace tvspec {
 
-// Float32 storage of p: each pixel's dual value is held in registers as hi + lo (Fast2Sum
-// compensation of the update, chambolle_math.cuh), and lo is folded into hi after every
-// iteration i (0-based within an ROF step) with (i + 1) % kFold == 0 and after the step's last
-// iteration. Every launch therefore starts and ends at a fold point (iterations per launch are
+// Float32 storage of p: each pixel's dual value is held in registers as hi + lo (the
+// compensated update of chambolle_math.cuh: lo accumulates the increments, the iteration reads
+// fl(hi + lo)), and lo is folded into hi after every iteration i (0-based within an ROF step)
+// with (i + 1) % kFold == 0 and after the step's last iteration. Every launch therefore starts and ends at a fold point (iterations per launch are
 // multiples of kFold), p is stored as one float32 per component, and the results do not depend
 // on the tile shape or the iterations per launch.
 constexpr int kFold = 4;
