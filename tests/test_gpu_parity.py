@@ -110,22 +110,24 @@ def test_every_tile_shape_and_depth_bit_identical(tv, H, W):
             _same(out, base)
 
 
-def test_many_waves_of_tiles_bit_identical_and_parity(tv):
+# 1000 x 1100: edge-aligned tiles for every shape; 1001 x 999 (odd width): masked border tiles
+@pytest.mark.parametrize("H,W", [(1000, 1100), (1001, 999)])
+def test_many_waves_of_tiles_bit_identical_and_parity(tv, H, W):
     # an image with many more tiles than the GPU holds at once: later tiles read halos that
     # earlier tiles of the same launch have already finished (the ping-pong copies of p must
     # make that irrelevant), and the run must be reproducible
-    f = syn.make_image(1000, 1100, 120, (2.0, 60.0), (0.05, 1.0), 0.02, seed=77)
+    f = syn.make_image(H, W, 120, (2.0, 60.0), (0.05, 1.0), 0.02, seed=77 + H - 1000)
     args = (f, 0.5, 3, 40, syn.DYADIC_EDGES)
     with tv.Plan(0, kernel=tv.KERNEL_NAIVE) as p:
         base = p.decompose(*args, trace=True)
-    for tile in (0, 5, 10, 11):
+    for tile in (0, 5, 8, 10, 11, 24):  # 8 and 24: the shapes the autotuner picks for large and 512^2 images
         with tv.Plan(0, kernel=tv.KERNEL_TILED, tile=tile) as p:
             a = p.decompose(*args, trace=True)
             b = p.decompose(*args, trace=True)
         _same(a, base)
         _same(b, base)
     ref = oracle.decompose(*args, trace=True)
-    assert_parity(base, ref, f, "1000x1100")
+    assert_parity(base, ref, f, f"{H}x{W}")
 
 
 def test_graph_and_plain_launches_bit_identical(tv):
