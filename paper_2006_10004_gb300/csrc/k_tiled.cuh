@@ -92,12 +92,12 @@ struct GlShared {
 // (for the divergence of its first row) and wn of the first row of warp wy + 1 (for the
 // gradient of its last row); its other rows need only its own registers. So each iteration
 // computes wn on rows 1..R-1 first, then on row 0 with p1 from above, and hands its wn row 0
-// up; it updates rows 0..R-2 first, then row R-1 with wn from below, and hands its p1 row R-1
-// down; two CTA barriers per iteration order the hand-offs. (Measured: this order is faster
-// than rows in sequence, and faster than pairwise named barriers between neighbouring warps,
-// which let a warp wait for its neighbours only.) The function writes its first hand-off row
-// itself; callers separate two calls by a CTA barrier (the exchange rows are reused). A call
-// with n_iter <= 0 does nothing.
+// up; then, with wn from below read, it updates all rows and hands its p1 row R-1 down; two
+// CTA barriers per iteration order the hand-offs. (Measured: this order is faster than rows in
+// sequence in both phases and than putting the exchanged row last in both; faster too than
+// pairwise named barriers between neighbouring warps, which let a warp wait for its neighbours
+// only.) The function writes its first hand-off row itself; callers separate two calls by a CTA
+// barrier (the exchange rows are reused). A call with n_iter <= 0 does nothing.
 template <int V, int R, int RW, bool FAST, int EDGE, bool ZERO_LEFT = false, bool COMP = false,
           class GL>
 __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (&p2)[R][V / 2],
@@ -204,10 +204,8 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
             put_row(s_wt[wy], w[0]);
             __syncthreads();
         }
-        // ---- the update on rows 0..R-2, then on row R-1 with wn from the warp below (the
-        // tile's last row: a halo row, or the image's last row, whose G1 is masked)
-#pragma unroll
-        for (int r = 0; r < R - 1; ++r) update_row(r, w[r + 1]);
+        // ---- the update on every row, row R-1 with wn from the warp below (the tile's last
+        // row: a halo row, or the image's last row, whose G1 is masked)
         float2 dn[VP];
         if (RW > 1 && wy < RW - 1) {
             get_row(s_wt[wy + 1], dn);
@@ -215,7 +213,8 @@ __device__ __forceinline__ void tiled_iterate_g(float2 (&p1)[R][V / 2], float2 (
 #pragma unroll
             for (int j = 0; j < VP; ++j) dn[j] = w[R - 1][j];
         }
-        update_row(R - 1, dn);
+#pragma unroll
+        for (int r = 0; r < R; ++r) update_row(r, r < R - 1 ? w[r + 1] : dn);
         if constexpr (COMP) {
             const int done = it0 + it + 1;  // iterations of the step completed
             if (done % kFold == 0 || done == n_total) {  // uniform over the CTA
