@@ -129,8 +129,11 @@ typedef struct {
                                memory per CTA, completing on an mbarrier whose wait is bounded:
                                a wait that runs out fails the call with TVSPEC_ETIMEOUT) for
                                the tile shapes that allow it (float32 p, 16-byte aligned tile
-                               columns, tile in static shared memory: shapes 8, 24, 25); other
-                               shapes and batches keep per-thread loads. Same bits either way.
+                               columns, tile in static shared memory: shapes 8, 24, 25) and
+                               images whose tile columns all start on 4 floats (with tiles
+                               aligned to the image border, the last column of tiles starts at
+                               W - 64: W a multiple of 4); other shapes, images and batches keep
+                               per-thread loads. Same bits either way.
                                0 (default): per-thread loads. */
 } tvspec_config;
 
